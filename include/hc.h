@@ -1,0 +1,258 @@
+/*
+ * hc.h -- C ABI of the GB300 concurrent hash-container library (libhc.so).
+ *
+ * The containers are the hash-based collections of "stdgpu: Efficient
+ * STL-like Data Structures on the GPU" (Stotko, 2019), Section 4.1: an
+ * unordered_set keeps keys, an unordered_map keeps a key and its mapped
+ * value, and each key is held at most once.  Capacity is fixed when the
+ * container is created (Section 4, "Capacity"); the range forms of insert,
+ * erase, find and contains (Section 4.1) run over whole device arrays with a
+ * result per key; inserting beyond the capacity is the only failure
+ * (Section 4, "Guarantees").
+ *
+ * Conventions for every call below:
+ *   - Data pointers named d_* are DEVICE pointers on the table's device,
+ *     owned by the caller (for example torch tensors); the library never
+ *     frees or keeps them after the call's work has run.  Inputs and outputs
+ *     must not alias.  Key arrays must be aligned to the key size, value
+ *     arrays to the value size.
+ *   - Pointers named h_* are HOST pointers (pinned memory gives overlap).
+ *   - Counts are signed 64-bit (Section 3.2 chooses a signed index type);
+ *     n < 0 is an argument error, n == 0 is a no-op returning HC_OK.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls are asynchronous and ordered on `stream` unless their
+ *     comment says they synchronise.  Work on one table must be ordered by
+ *     the caller (one stream, or events): calls on one table are phases, and
+ *     each call is one concurrent batch.
+ *   - Argument errors return before anything is launched.  On error the
+ *     return code is not HC_OK and hc_last_error() describes it.
+ *   - Handles are not safe for concurrent host calls on the same table.
+ *
+ * Key types: uint32 (HC_SET_U32), uint64 (HC_SET_U64, HC_MAP_U64_U64) and
+ * int64 (HC_MAP_I64_I32).  Every bit pattern is a valid key: the paper's
+ * containers avoid placeholder values (Section 5.1).  The two largest bit
+ * patterns of the key type (all ones, all ones minus one) are held in two side
+ * slots of the table header, so they never use one of the `slots`.
+ */
+#ifndef HC_H
+#define HC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HC_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define HC_API __attribute__((visibility("default")))
+#else
+#define HC_API
+#endif
+
+typedef struct hc_table hc_table;
+typedef struct hc_batch hc_batch;
+
+/* Container kinds (Section 4.1: set = keys only, map = key -> mapped value). */
+typedef enum hc_kind {
+    HC_SET_U32 = 0,      /* unordered_set<uint32>                       */
+    HC_SET_U64 = 1,      /* unordered_set<uint64>                       */
+    HC_MAP_I64_I32 = 2,  /* unordered_map<int64, int32>                 */
+    HC_MAP_U64_U64 = 3   /* unordered_map<uint64, uint64>               */
+} hc_kind;
+
+/* Return codes. */
+typedef enum hc_rc {
+    HC_OK = 0,
+    HC_ERR_ARG = 1,       /* invalid argument; nothing launched          */
+    HC_ERR_OOM = 2,       /* device allocation failed                    */
+    HC_ERR_OVERFLOW = 3,  /* an insert found the table full (sticky)     */
+    HC_ERR_CUDA = 4,      /* a CUDA runtime call failed                  */
+    HC_ERR_STATE = 5      /* a device-side bound was hit (see hc_stats)  */
+} hc_rc;
+
+/* Per-key status bytes written by insert and erase. */
+enum {
+    HC_INSERTED = 0,   /* key was absent and is now stored                */
+    HC_EXISTS = 1,     /* key was already stored; its value is unchanged  */
+    HC_OVERFLOW = 2,   /* key was absent and the table is full            */
+    HC_ERASED = 3,     /* key was stored and is now removed               */
+    HC_NOT_FOUND = 4   /* key was not stored                              */
+};
+
+/* Operation codes for batches and launch shapes. */
+enum { HC_OP_INSERT = 0, HC_OP_FIND = 1, HC_OP_ERASE = 2 };
+
+/* Bucket hash.  HC_HASH_MIX64 is a 64-bit finaliser of (key ^ seed) reduced
+ * by a 64x64 high multiply; HC_HASH_TESCHNER is the spatial hash of Section
+ * 4.1 (coordinates times 73856093, 19349669, 83492791, combined by xor,
+ * reduced modulo the bucket count) applied to keys that pack three signed
+ * 21-bit block coordinates as x | y << 21 | z << 42 (HC_MAP_I64_I32 only).
+ * The hash never changes a result, only where keys are stored. */
+enum { HC_HASH_MIX64 = 0, HC_HASH_TESCHNER = 1 };
+
+/* Layout chosen at creation.  Zero fields take the defaults. */
+typedef struct hc_config {
+    int32_t bucket_bytes;  /* 32, 64 or 128 (default 32): one probe reads one
+                              bucket; buckets are aligned to 32-byte sectors */
+    int32_t hash_mode;     /* HC_HASH_*; default HC_HASH_MIX64             */
+    uint64_t seed;         /* hash seed (default 0)                        */
+} hc_config;
+
+/* Launch shape of one operation.  A group of bucket_bytes / lane_bytes
+ * lanes probes a bucket together; each group handles keys_per_group keys at
+ * once so that several bucket reads are in flight per lane.  Zero fields
+ * keep the current value.  Results never depend on the shape. */
+typedef struct hc_launch {
+    int32_t lane_bytes;       /* 16 or 32, at most bucket_bytes          */
+    int32_t keys_per_group;   /* 1, 2 or 4                               */
+    int32_t block;            /* threads per block: 64..512, multiple of 32  */
+    int32_t fold_duplicates;  /* 1: equal keys inside a warp are folded to
+                                 one probe (__match_any_sync); 2: off      */
+} hc_launch;
+
+/* Counters read back by hc_stats (synchronising). */
+typedef struct hc_stats_t {
+    int64_t live;            /* stored keys (Section 4.1 size)               */
+    int64_t used;            /* slots not EMPTY: stored keys + tombstones,
+                                excluding the two side slots                  */
+    int64_t capacity;        /* slots, as requested at create / rehash       */
+    int64_t slot_bytes;      /* bytes per slot                               */
+    int64_t table_bytes;     /* device bytes held by the table               */
+    uint32_t error_bits;     /* 1 = an insert overflowed, 2 = probe bound hit */
+    uint32_t reserved;
+} hc_stats_t;
+
+/* Library ABI version (HC_ABI_VERSION). */
+HC_API int32_t hc_abi_version(void);
+
+/* Message for the last error returned on this host thread ("" if none). */
+HC_API const char *hc_last_error(void);
+
+/* Device bytes a table of `slots` slots would hold (for memory budgets).
+ * Fixed capacity, Section 4. */
+HC_API hc_rc hc_table_bytes(int32_t kind, int64_t slots, const hc_config *cfg, int64_t *bytes);
+
+/* Create a container with a fixed capacity of `slots` slots (Section 4,
+ * "Capacity"; Section 3.7, explicit create/destroy of device objects).  The
+ * slot array is allocated on the current device with cudaMalloc and
+ * initialised to empty on `stream`.  slots >= 1.  *out receives the handle. */
+HC_API hc_rc hc_create(hc_table **out, int32_t kind, int64_t slots, const hc_config *cfg, void *stream);
+
+/* Destroy a table and free its device memory.  Synchronises the device
+ * first so no queued work still uses it.  NULL is a no-op. */
+HC_API hc_rc hc_destroy(hc_table *t);
+
+/* Set the launch shape of one operation (HC_OP_*) on this table. */
+HC_API hc_rc hc_set_launch(hc_table *t, int32_t op, const hc_launch *shape);
+HC_API hc_rc hc_get_launch(const hc_table *t, int32_t op, hc_launch *shape);
+
+/* Range insert (Section 4.1, insert): for i < n, insert d_keys[i] (and
+ * d_vals[i] for maps; NULL for sets).  d_status[i] (nullable) receives
+ * HC_INSERTED, HC_EXISTS (present already: stored value unchanged) or
+ * HC_OVERFLOW (absent and no free slot: the only failure, Section 4).
+ * Equal keys inside one batch: exactly one position gets HC_INSERTED when
+ * the key was absent and fits, the others HC_EXISTS; which one is not
+ * specified.  An overflow also sets the table's sticky error bit. */
+HC_API hc_rc hc_insert(hc_table *t, const void *d_keys, const void *d_vals, int64_t n,
+                uint8_t *d_status, void *stream);
+
+/* Range find / contains (Section 4.1): d_found[i] = 1 if d_keys[i] is
+ * stored, else 0.  For maps, d_vals_out[i] (nullable: contains only)
+ * receives the mapped value, or 0 when absent.  Lookups take no lock. */
+HC_API hc_rc hc_find(hc_table *t, const void *d_keys, int64_t n, uint8_t *d_found,
+              void *d_vals_out, void *stream);
+
+/* Range erase (Section 4.1): d_status[i] (nullable) receives HC_ERASED or
+ * HC_NOT_FOUND.  Equal keys in one batch: one HC_ERASED at most.  An erased
+ * slot becomes a tombstone that later inserts reuse. */
+HC_API hc_rc hc_erase(hc_table *t, const void *d_keys, int64_t n, uint8_t *d_status,
+               void *stream);
+
+/* Host-buffer forms of the three range calls: keys, values and results are
+ * HOST arrays.  The library copies them in chunks through device staging
+ * buffers that the table allocates on first use and keeps, overlapping the
+ * copies with the kernels.  They return after the results are on the host
+ * (synchronising `stream`). */
+HC_API hc_rc hc_insert_host(hc_table *t, const void *h_keys, const void *h_vals, int64_t n,
+                     uint8_t *h_status, void *stream);
+HC_API hc_rc hc_find_host(hc_table *t, const void *h_keys, int64_t n, uint8_t *h_found,
+                   void *h_vals_out, void *stream);
+HC_API hc_rc hc_erase_host(hc_table *t, const void *h_keys, int64_t n, uint8_t *h_status,
+                    void *stream);
+
+/* Number of stored keys (Section 4.1).  Synchronises `stream`. */
+HC_API hc_rc hc_size(hc_table *t, int64_t *live, void *stream);
+
+/* All counters (synchronises `stream`). */
+HC_API hc_rc hc_stats(hc_table *t, hc_stats_t *out, void *stream);
+
+/* HC_ERR_OVERFLOW if an insert overflowed since the last call, HC_ERR_STATE
+ * if a device-side bound was hit, else HC_OK; clears the sticky bits.
+ * Synchronises `stream`. */
+HC_API hc_rc hc_status(hc_table *t, void *stream);
+
+/* Remove every key (the table returns to its state after create). */
+HC_API hc_rc hc_clear(hc_table *t, void *stream);
+
+/* Manual resize on the host (Section 4, "Capacity"): move the stored keys
+ * into a new slot array of `new_slots` slots (which may equal the current
+ * capacity: this purges tombstones).  HC_ERR_ARG if new_slots is below the
+ * number of stored keys that use a slot.  Synchronises `stream`; the old
+ * array is freed before returning. */
+HC_API hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream);
+
+/* Copy the stored keys (and values for maps; d_vals_out may be NULL) into
+ * device arrays of `cap` entries, in unspecified order (Section 3.6, a range
+ * over a container's stored entries).  *n_out receives the number of stored
+ * keys; if it exceeds cap only cap entries are written and HC_ERR_ARG is
+ * returned.  Synchronises `stream`. */
+HC_API hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap,
+              int64_t *n_out, void *stream);
+
+/* ---- batched form: many tables in one persistent launch -----------------
+ * Not in the paper (it has one container per call); it schedules many of the
+ * Section 4.1 range calls at once.  A batch holds items; each item is one
+ * range call (op, table, arrays) exactly as in hc_insert / hc_find /
+ * hc_erase.  The batch runs as three phases -- all insert items, then all
+ * find items, then all erase items -- each phase one persistent kernel in
+ * which warps take fixed-size tiles of any item from a shared counter.  Items
+ * on the same table in the same phase form one concurrent batch. */
+typedef struct hc_batch_item {
+    hc_table *table;
+    int32_t op;            /* HC_OP_*                                      */
+    int32_t reserved;
+    const void *d_keys;
+    const void *d_vals;    /* insert into a map: values; else NULL         */
+    int64_t n;
+    uint8_t *d_out;        /* insert/erase: status (nullable); find: found */
+    void *d_vals_out;      /* find on a map: values (nullable)             */
+} hc_batch_item;
+
+typedef struct hc_batch_config {
+    int32_t lane_bytes;      /* as hc_launch; 0 = each table's own shape   */
+    int32_t keys_per_group;
+    int32_t block;           /* threads per block (0 = 256)                */
+    int32_t blocks_per_sm;   /* persistent grid = SMs x this (0 = auto)    */
+    int32_t tile;            /* keys per tile (0 = auto)                   */
+    int32_t use_graph;       /* 1: capture the three phases in a CUDA graph */
+} hc_batch_config;
+
+/* Build a batch over `n_items` items (copied; the arrays they point to must
+ * stay valid while the batch is used).  With use_graph the three phase
+ * kernels are captured once into a CUDA graph on `stream`. */
+HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t n_items,
+                      const hc_batch_config *cfg, void *stream);
+
+/* Run a batch on `stream` (a graph launch when captured). */
+HC_API hc_rc hc_batch_launch(hc_batch *b, void *stream);
+
+/* Destroy a batch (synchronises the device first). */
+HC_API hc_rc hc_batch_destroy(hc_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HC_H */

@@ -1,0 +1,118 @@
+"""ctypes binding of libhc.so (the C ABI in include/hc.h).
+
+Argument marshalling only: every step of every call runs in the library's
+CUDA kernels.  Loading fails loudly when the library has not been built;
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhc.so")
+
+# hc_kind
+SET_U32, SET_U64, MAP_I64_I32, MAP_U64_U64 = 0, 1, 2, 3
+# hc_rc
+OK, ERR_ARG, ERR_OOM, ERR_OVERFLOW, ERR_CUDA, ERR_STATE = 0, 1, 2, 3, 4, 5
+RC_NAMES = {0: "HC_OK", 1: "HC_ERR_ARG", 2: "HC_ERR_OOM", 3: "HC_ERR_OVERFLOW", 4: "HC_ERR_CUDA", 5: "HC_ERR_STATE"}
+# per-key status
+INSERTED, EXISTS, OVERFLOW, ERASED, NOT_FOUND = 0, 1, 2, 3, 4
+# ops, hash modes
+OP_INSERT, OP_FIND, OP_ERASE = 0, 1, 2
+HASH_MIX64, HASH_TESCHNER = 0, 1
+
+EXPORTS = [
+    "hc_abi_version", "hc_last_error", "hc_table_bytes", "hc_create", "hc_destroy", "hc_set_launch",
+    "hc_get_launch", "hc_insert", "hc_find", "hc_erase", "hc_insert_host", "hc_find_host", "hc_erase_host",
+    "hc_size", "hc_stats", "hc_status", "hc_clear", "hc_rehash", "hc_dump", "hc_batch_create",
+    "hc_batch_launch", "hc_batch_destroy",
+]
+
+
+class HCError(RuntimeError):
+    def __init__(self, rc: int, msg: str):
+        super().__init__(f"{RC_NAMES.get(rc, rc)}: {msg}")
+        self.rc = rc
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("bucket_bytes", ctypes.c_int32), ("hash_mode", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class Launch(ctypes.Structure):
+    _fields_ = [("lane_bytes", ctypes.c_int32), ("keys_per_group", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("fold_duplicates", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("live", ctypes.c_int64), ("used", ctypes.c_int64), ("capacity", ctypes.c_int64),
+                ("slot_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64), ("error_bits", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_void_p), ("op", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("d_keys", ctypes.c_void_p), ("d_vals", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("d_out", ctypes.c_void_p), ("d_vals_out", ctypes.c_void_p)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("lane_bytes", ctypes.c_int32), ("keys_per_group", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "hc_abi_version": (i32, []),
+        "hc_last_error": (ctypes.c_char_p, []),
+        "hc_table_bytes": (i32, [i32, i64, P(Config), P(i64)]),
+        "hc_create": (i32, [P(vp), i32, i64, P(Config), vp]),
+        "hc_destroy": (i32, [vp]),
+        "hc_set_launch": (i32, [vp, i32, P(Launch)]),
+        "hc_get_launch": (i32, [vp, i32, P(Launch)]),
+        "hc_insert": (i32, [vp, vp, vp, i64, vp, vp]),
+        "hc_find": (i32, [vp, vp, i64, vp, vp, vp]),
+        "hc_erase": (i32, [vp, vp, i64, vp, vp]),
+        "hc_insert_host": (i32, [vp, vp, vp, i64, vp, vp]),
+        "hc_find_host": (i32, [vp, vp, i64, vp, vp, vp]),
+        "hc_erase_host": (i32, [vp, vp, i64, vp, vp]),
+        "hc_size": (i32, [vp, P(i64), vp]),
+        "hc_stats": (i32, [vp, P(Stats), vp]),
+        "hc_status": (i32, [vp, vp]),
+        "hc_clear": (i32, [vp, vp]),
+        "hc_rehash": (i32, [vp, i64, vp]),
+        "hc_dump": (i32, [vp, vp, vp, i64, P(i64), vp]),
+        "hc_batch_create": (i32, [P(vp), P(BatchItem), i64, P(BatchConfig), vp]),
+        "hc_batch_launch": (i32, [vp, vp]),
+        "hc_batch_destroy": (i32, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhc.so.  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"libhc.so is not built ({path}); run `python -m paper_1908_05936_gb300.build`")
+            _lib = _declare(ctypes.CDLL(path))
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != OK:
+        raise HCError(rc, load().hc_last_error().decode())

@@ -1,0 +1,314 @@
+// hc_batch.cu -- the batched form: many range calls on many tables in one
+// persistent launch per phase (insert, then find, then erase), optionally
+// captured once into a CUDA graph and replayed.
+//
+// Scheduling.  Every item is cut into chunks of `tile` keys.  A phase kernel
+// runs a persistent grid (SMs x blocks per SM); each warp takes the next
+// chunk number from a counter in global memory with one atomic add, finds the
+// item that chunk belongs to by binary search over the items' chunk offsets,
+// and runs the same warp-tile code as the one-launch-per-call kernels over
+// the chunk.  Tables of very different sizes are therefore balanced at chunk
+// granularity, and no launch is spent per table.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hc.h"
+#include "hc_core.cuh"
+#include "hc_internal.h"
+#include "hc_table.h"
+
+namespace hc {
+
+struct BatchItemDev {
+    View v;
+    const void *keys;
+    const void *vals;
+    uint8_t *out;
+    void *vals_out;
+    long long n;
+    long long chunk_begin;   // first chunk number of this item within its phase
+    int bb;
+    int fold;
+};
+
+// Work of one phase launch: items [item0, item0 + n_items) of one kind.
+struct PhaseDesc {
+    int kind;
+    int op;
+    int item0;
+    int n_items;
+    long long n_chunks;
+    int counter;   // index of this phase's chunk counter
+};
+
+template <int KIND, int OP, int BB, int LB, int KPT>
+__device__ __forceinline__ void run_chunk(const BatchItemDev &it, long long k0, long long k1) {
+    using T = Traits<KIND>;
+    constexpr int TILE = Shape<BB, LB, KPT>::TILE;
+    for (long long base = k0; base < k1; base += TILE) {
+        // keys past the chunk end belong to the next chunk: clamp n to it
+        if constexpr (OP == OP_INSERT)
+            insert_tile<KIND, BB, LB, KPT>(it.v, (const typename T::Key *)it.keys, (const typename T::Val *)it.vals,
+                                           k1, it.out, base, it.fold != 0);
+        else if constexpr (OP == OP_FIND)
+            find_tile<KIND, BB, LB, KPT>(it.v, (const typename T::Key *)it.keys, k1, it.out,
+                                         (typename T::Val *)it.vals_out, base);
+        else
+            erase_tile<KIND, BB, LB, KPT>(it.v, (const typename T::Key *)it.keys, k1, it.out, base, it.fold != 0);
+    }
+}
+
+template <int KIND, int OP, int LB, int KPT>
+__global__ void __launch_bounds__(256)
+k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_chunks, int tile,
+              unsigned long long *counter) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(counter, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if ((long long)c >= n_chunks) break;
+        // last item whose chunk_begin <= c
+        int lo = 0, hi = n_items - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].chunk_begin <= (long long)c) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchItemDev it = items[lo];
+        const long long k0 = ((long long)c - it.chunk_begin) * tile;
+        const long long k1 = k0 + tile < it.n ? k0 + tile : it.n;
+        switch (it.bb) {
+            case 32: run_chunk<KIND, OP, 32, LB, KPT>(it, k0, k1); break;
+            case 64: run_chunk<KIND, OP, 64, LB, KPT>(it, k0, k1); break;
+            default: run_chunk<KIND, OP, 128, LB, KPT>(it, k0, k1); break;
+        }
+    }
+}
+
+__global__ void k_zero_counters(unsigned long long *c, int n) {
+    if (threadIdx.x < n) c[threadIdx.x] = 0ull;
+}
+
+using PhaseKernel = void (*)(const BatchItemDev *, int, long long, int, unsigned long long *);
+
+template <int KIND, int OP>
+PhaseKernel pick_lb_kpt(int lb, int kpt) {
+    if (lb == 16) {
+        if (kpt == 1) return k_batch_phase<KIND, OP, 16, 1>;
+        if (kpt == 2) return k_batch_phase<KIND, OP, 16, 2>;
+        return k_batch_phase<KIND, OP, 16, 4>;
+    }
+    if (kpt == 1) return k_batch_phase<KIND, OP, 32, 1>;
+    if (kpt == 2) return k_batch_phase<KIND, OP, 32, 2>;
+    return k_batch_phase<KIND, OP, 32, 4>;
+}
+
+template <int KIND>
+PhaseKernel pick_op(int op, int lb, int kpt) {
+    if (op == OP_INSERT) return pick_lb_kpt<KIND, OP_INSERT>(lb, kpt);
+    if (op == OP_FIND) return pick_lb_kpt<KIND, OP_FIND>(lb, kpt);
+    return pick_lb_kpt<KIND, OP_ERASE>(lb, kpt);
+}
+
+PhaseKernel pick_kernel(int kind, int op, int lb, int kpt) {
+    switch (kind) {
+        case KIND_SET_U32: return pick_op<KIND_SET_U32>(op, lb, kpt);
+        case KIND_SET_U64: return pick_op<KIND_SET_U64>(op, lb, kpt);
+        case KIND_MAP_I64_I32: return pick_op<KIND_MAP_I64_I32>(op, lb, kpt);
+        default: return pick_op<KIND_MAP_U64_U64>(op, lb, kpt);
+    }
+}
+
+}  // namespace hc
+
+struct hc_batch {
+    uint32_t magic;
+    int device;
+    int block, blocks_per_sm, tile, lane_bytes, kpt;
+    bool use_graph;
+    void *d_mem = nullptr;   // items then counters
+    hc::BatchItemDev *d_items = nullptr;
+    unsigned long long *d_counters = nullptr;
+    std::vector<hc::PhaseDesc> phases;
+    std::vector<int> grid;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+// Errors go to the same thread-local message as the rest of the API (owned
+// by hc_api.cu).
+hc_rc hc_internal_fail(hc_rc rc, const char *msg);
+
+namespace {
+
+constexpr uint32_t kBatchMagic = 0x48434241u;
+
+hc_rc bfail(hc_rc rc, const std::string &msg) { return hc_internal_fail(rc, msg.c_str()); }
+
+hc_rc bcuda(cudaError_t e, const char *what) {
+    return bfail(HC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+hc_rc enqueue(hc_batch *b, cudaStream_t s) {
+    const int n_ctr = (int)b->phases.size();
+    if (n_ctr == 0) return HC_OK;
+    hc::k_zero_counters<<<1, 32, 0, s>>>(b->d_counters, n_ctr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bcuda(e, "resetting the batch counters");
+    for (size_t p = 0; p < b->phases.size(); ++p) {
+        const hc::PhaseDesc &ph = b->phases[p];
+        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, b->lane_bytes, b->kpt);
+        k<<<b->grid[p], b->block, 0, s>>>(b->d_items + ph.item0, ph.n_items, ph.n_chunks, b->tile,
+                                          b->d_counters + ph.counter);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(e, "launching a batch phase");
+    }
+    return HC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg,
+                             void *stream) {
+    if (!out) return bfail(HC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_items < 0 || (n_items > 0 && !items)) return bfail(HC_ERR_ARG, "bad item list");
+    hc_batch_config c{};
+    if (cfg) c = *cfg;
+    const int lb = c.lane_bytes ? c.lane_bytes : 32;
+    const int kpt = c.keys_per_group ? c.keys_per_group : 2;
+    const int block = c.block ? c.block : 256;
+    const int tile = c.tile ? c.tile : 4096;
+    if (lb != 16 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 16 or 32");
+    if (kpt != 1 && kpt != 2 && kpt != 4) return bfail(HC_ERR_ARG, "keys_per_group must be 1, 2 or 4");
+    if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
+    if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
+
+    // items ordered by (op, kind) so each phase launch sees one contiguous run
+    std::vector<hc::BatchItemDev> dev;
+    std::vector<hc::PhaseDesc> phases;
+    for (int op = 0; op < 3; ++op) {
+        for (int kind = 0; kind < 4; ++kind) {
+            hc::PhaseDesc ph{kind, op, (int)dev.size(), 0, 0, (int)phases.size()};
+            for (int64_t i = 0; i < n_items; ++i) {
+                const hc_batch_item &it = items[i];
+                if (!it.table || it.table->magic != HC_TABLE_MAGIC) return bfail(HC_ERR_ARG, "item with a bad table");
+                if (it.op < 0 || it.op > 2) return bfail(HC_ERR_ARG, "item with a bad op");
+                if (it.n < 0) return bfail(HC_ERR_ARG, "item with n < 0");
+                if (it.op != op || it.table->kind != kind || it.n == 0) continue;
+                const bool map = kind >= HC_MAP_I64_I32;
+                const int kb = kind == HC_SET_U32 ? 4 : 8;
+                if (!it.d_keys || reinterpret_cast<uintptr_t>(it.d_keys) % kb)
+                    return bfail(HC_ERR_ARG, "item keys NULL or misaligned");
+                if (op == HC_OP_INSERT && map && !it.d_vals) return bfail(HC_ERR_ARG, "insert item on a map without values");
+                if (op == HC_OP_FIND && !it.d_out) return bfail(HC_ERR_ARG, "find item without a found array");
+                if (lb > it.table->bucket_bytes) return bfail(HC_ERR_ARG, "lane_bytes exceeds an item's bucket size");
+                hc::BatchItemDev d{};
+                d.v = it.table->view;
+                d.keys = it.d_keys;
+                d.vals = map ? it.d_vals : nullptr;
+                d.out = it.d_out;
+                d.vals_out = map ? it.d_vals_out : nullptr;
+                d.n = it.n;
+                d.chunk_begin = ph.n_chunks;
+                d.bb = it.table->bucket_bytes;
+                d.fold = op == HC_OP_FIND ? 0 : it.table->shape[op].fold;
+                ph.n_chunks += (it.n + tile - 1) / tile;
+                dev.push_back(d);
+                ph.n_items++;
+            }
+            if (ph.n_items) phases.push_back(ph);
+        }
+    }
+
+    hc_batch *b = new hc_batch();
+    b->magic = kBatchMagic;
+    b->block = block;
+    b->tile = tile;
+    b->lane_bytes = lb;
+    b->kpt = kpt;
+    b->use_graph = c.use_graph != 0;
+    b->phases = phases;
+    cudaError_t e = cudaGetDevice(&b->device);
+    const size_t items_bytes = (dev.size() * sizeof(hc::BatchItemDev) + 255) / 256 * 256;
+    const size_t bytes = items_bytes + 256;
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_mem, bytes);
+    if (e != cudaSuccess) {
+        delete b;
+        return bcuda(e, "allocating the batch descriptors");
+    }
+    b->d_items = static_cast<hc::BatchItemDev *>(b->d_mem);
+    b->d_counters = reinterpret_cast<unsigned long long *>(static_cast<char *>(b->d_mem) + items_bytes);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!dev.empty())
+        e = cudaMemcpyAsync(b->d_items, dev.data(), dev.size() * sizeof(hc::BatchItemDev), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    for (size_t p = 0; p < phases.size() && e == cudaSuccess; ++p) {
+        int per_sm = c.blocks_per_sm;
+        if (per_sm <= 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, hc::pick_kernel(phases[p].kind, phases[p].op, lb, kpt), block, 0);
+            if (per_sm <= 0) per_sm = 1;
+        }
+        long long g = (long long)sms * per_sm;
+        const long long need = (phases[p].n_chunks * 32 + block - 1) / block;   // one warp per chunk at most
+        if (g > need) g = need;
+        b->grid.push_back((int)(g > 0 ? g : 1));
+    }
+    if (e == cudaSuccess && b->use_graph) {
+        // capture on a private stream so the caller's stream is never in capture mode
+        cudaStream_t cs;
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            hc_rc rc = HC_OK;
+            if (e == cudaSuccess) rc = enqueue(b, cs);
+            cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+            if (e == cudaSuccess) e = e2;
+            if (rc != HC_OK && e == cudaSuccess) e = cudaErrorUnknown;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            cudaStreamDestroy(cs);
+        }
+    }
+    if (e != cudaSuccess) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        cudaFree(b->d_mem);
+        delete b;
+        return bcuda(e, "building the batch");
+    }
+    *out = b;
+    return HC_OK;
+}
+
+HC_API hc_rc hc_batch_launch(hc_batch *b, void *stream) {
+    if (!b || b->magic != kBatchMagic) return bfail(HC_ERR_ARG, "invalid batch handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (b->exec) {
+        cudaError_t e = cudaGraphLaunch(b->exec, s);
+        if (e != cudaSuccess) return bcuda(e, "launching the batch graph");
+        return HC_OK;
+    }
+    return enqueue(b, s);
+}
+
+HC_API hc_rc hc_batch_destroy(hc_batch *b) {
+    if (!b) return HC_OK;
+    if (b->magic != kBatchMagic) return bfail(HC_ERR_ARG, "invalid batch handle");
+    b->magic = 0;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaError_t e = cudaFree(b->d_mem);
+    delete b;
+    if (e != cudaSuccess) return bcuda(e, "cudaFree");
+    return HC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,702 @@
+// hc_core.cuh -- device side of the GB300 hash containers.
+//
+// Layout.  A table is an array of nb buckets of BB bytes (32, 64 or 128),
+// each aligned to a 32-byte sector, holding BB / SLOT slots in
+// array-of-structures order:
+//   set<u32>       4-byte slot  = key
+//   set<u64>       8-byte slot  = key
+//   map<i64,i32>  16-byte slot  = key (8) | value (4) | padding (4)
+//   map<u64,u64>  16-byte slot  = key (8) | value (8)
+// A slot is EMPTY (all-ones key), a TOMBSTONE (all-ones minus one) or holds a
+// key.  The two keys whose bit patterns equal those markers live in two side
+// slots of the header instead (every bit pattern is a valid key: the paper
+// avoids placeholder keys, Section 5.1).  Slots past the requested capacity in
+// the last bucket are written as tombstones at clear time, so a table never
+// stores more than `capacity` keys in slots (fixed capacity, Section 4).
+//
+// Probing.  A key hashes to a first bucket; buckets are visited in order,
+// wrapping around, at most nb of them.  A group of G = BB / LB lanes reads one
+// bucket together (each lane LB = 16 or 32 bytes, one vector load) and
+// combines its findings with __ballot_sync.  Each group works on KPT keys at
+// once: the bucket loads for all of them are issued before any is examined, so
+// a lane keeps several independent sector reads in flight.
+//
+//   insert: stop at the key (EXISTS) or at the first bucket holding an EMPTY
+//           slot; claim the first free slot (EMPTY or TOMBSTONE) seen on the
+//           way with a compare-and-swap of the key; a lost race restarts the
+//           probe from the first bucket.  A full table (no free slot in nb
+//           buckets) gives OVERFLOW, the only failure (Section 4).
+//   find:   stop at the key or at a bucket holding an EMPTY slot; take no lock
+//           (lookups are non-blocking, Section 4).
+//   erase:  find, then swap the key for a TOMBSTONE with a compare-and-swap.
+//
+// Counters.  The header's live / used counters move by one atomic add per
+// warp (__reduce_add_sync of the lanes' counts).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hc {
+
+enum : int { KIND_SET_U32 = 0, KIND_SET_U64 = 1, KIND_MAP_I64_I32 = 2, KIND_MAP_U64_U64 = 3 };
+enum : uint32_t { ST_INSERTED = 0, ST_EXISTS = 1, ST_OVERFLOW = 2, ST_ERASED = 3, ST_NOT_FOUND = 4 };
+enum : uint32_t { ERR_OVERFLOW = 1u, ERR_PROBE_BOUND = 2u };
+enum : int { HASH_MIX64 = 0, HASH_TESCHNER = 1 };
+
+// Restarts of an insert probe after lost compare-and-swap races.  Each lost
+// race means another key took a slot, so this bound is never reached by a
+// correct table; it only keeps every loop finite.
+constexpr uint32_t kMaxRestarts = 1u << 16;
+
+// Device-resident table header (256 bytes, sits in front of the slots).
+struct alignas(256) Header {
+    unsigned long long live;             // stored keys, side slots included
+    unsigned long long used;             // slots that are not EMPTY (keys + tombstones)
+    unsigned int err;                    // sticky ERR_* bits
+    unsigned int side_present[2];        // [0]: all-ones key, [1]: all-ones-minus-one key
+    unsigned int pad0;
+    unsigned long long side_val[2];
+    unsigned long long dump_count;       // output cursor of the dump kernel
+    unsigned long long reinserted;       // counter of the rehash kernel
+};
+static_assert(sizeof(Header) == 256, "header is one 256-byte block");
+
+// What a kernel needs to reach a table; passed by value (Section 3.7: a
+// shallow copy of a device object can be handed to kernels).
+struct View {
+    unsigned char *slots;
+    Header *hdr;
+    unsigned long long nb;       // buckets
+    unsigned long long seed;
+    int hash_mode;
+    int pad;
+};
+
+template <int KIND> struct Traits;
+template <> struct Traits<KIND_SET_U32> {
+    using Key = uint32_t;
+    using Val = uint32_t;
+    static constexpr int SLOT = 4;
+    static constexpr bool MAP = false;
+    static constexpr Key EMPTY = 0xFFFFFFFFu, TOMB = 0xFFFFFFFEu;
+};
+template <> struct Traits<KIND_SET_U64> {
+    using Key = unsigned long long;
+    using Val = unsigned long long;
+    static constexpr int SLOT = 8;
+    static constexpr bool MAP = false;
+    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
+};
+template <> struct Traits<KIND_MAP_I64_I32> {
+    using Key = unsigned long long;   // int64 keys are handled as bit patterns
+    using Val = uint32_t;             // int32 values likewise
+    static constexpr int SLOT = 16;
+    static constexpr bool MAP = true;
+    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
+};
+template <> struct Traits<KIND_MAP_U64_U64> {
+    using Key = unsigned long long;
+    using Val = unsigned long long;
+    static constexpr int SLOT = 16;
+    static constexpr bool MAP = true;
+    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
+};
+
+// ------------------------------------------------------------------ hash ---
+
+// MurmurHash3's 64-bit finaliser (Appleby, public domain).
+__device__ __forceinline__ unsigned long long fmix64(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// Spatial hash of Section 4.1 on a key packing three signed 21-bit block
+// coordinates (x | y << 21 | z << 42).  The products are taken in unsigned
+// 64-bit wrap-around arithmetic, which is defined for every coordinate.
+__device__ __forceinline__ unsigned long long teschner(unsigned long long key) {
+    auto coord = [](unsigned long long v) -> unsigned long long {
+        long long c = (long long)(v & 0x1FFFFFull);
+        c = (c ^ 0x100000ll) - 0x100000ll;  // sign-extend 21 bits
+        return (unsigned long long)c;
+    };
+    unsigned long long x = coord(key), y = coord(key >> 21), z = coord(key >> 42);
+    return (x * 73856093ull) ^ (y * 19349669ull) ^ (z * 83492791ull);
+}
+
+__device__ __forceinline__ unsigned long long first_bucket(const View &v, unsigned long long key) {
+    if (v.hash_mode == HASH_TESCHNER) return teschner(key) % v.nb;
+    return __umul64hi(fmix64(key ^ v.seed), v.nb);
+}
+
+__device__ __forceinline__ unsigned long long next_bucket(const View &v, unsigned long long b) {
+    ++b;
+    return b == v.nb ? 0ull : b;
+}
+
+// --------------------------------------------------------------- memory ---
+
+// One lane's share of a bucket, LB bytes read with a single vector load that
+// is cached in L2 only (the slots are shared by all SMs and modified by
+// atomics; an L1 copy could be stale after a lost compare-and-swap).
+template <int LB> struct LaneWords;
+template <> struct LaneWords<16> {
+    unsigned long long w[2];
+    __device__ __forceinline__ void load(const unsigned char *p) {
+        asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(p));
+    }
+};
+template <> struct LaneWords<32> {
+    unsigned long long w[4];
+    __device__ __forceinline__ void load(const unsigned char *p) {
+        asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+                     : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
+    }
+};
+
+template <int KIND, int LB>
+__device__ __forceinline__ typename Traits<KIND>::Key slot_key(const LaneWords<LB> &lw, int s) {
+    using T = Traits<KIND>;
+    if constexpr (T::SLOT == 4) {
+        return (typename T::Key)(lw.w[s >> 1] >> ((s & 1) * 32));
+    } else if constexpr (T::SLOT == 8) {
+        return lw.w[s];
+    } else {
+        return lw.w[2 * s];
+    }
+}
+
+template <int KIND, int LB>
+__device__ __forceinline__ unsigned long long slot_val(const LaneWords<LB> &lw, int s) {
+    using T = Traits<KIND>;
+    if constexpr (T::MAP) {
+        if constexpr (sizeof(typename T::Val) == 4) return (uint32_t)lw.w[2 * s + 1];
+        else return lw.w[2 * s + 1];
+    } else {
+        return 0ull;
+    }
+}
+
+// 32- or 64-bit compare-and-swap on a slot's key.
+template <int KIND>
+__device__ __forceinline__ typename Traits<KIND>::Key cas_key(unsigned char *slot, typename Traits<KIND>::Key expect,
+                                                             typename Traits<KIND>::Key desired) {
+    if constexpr (sizeof(typename Traits<KIND>::Key) == 4)
+        return atomicCAS(reinterpret_cast<unsigned int *>(slot), expect, desired);
+    else
+        return atomicCAS(reinterpret_cast<unsigned long long *>(slot), expect, desired);
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_val(unsigned char *slot, unsigned long long val) {
+    using T = Traits<KIND>;
+    if constexpr (T::MAP) {
+        if constexpr (sizeof(typename T::Val) == 4) *reinterpret_cast<uint32_t *>(slot + 8) = (uint32_t)val;
+        else *reinterpret_cast<unsigned long long *>(slot + 8) = val;
+    }
+}
+
+// Streaming loads/stores of the caller's arrays (evict-first: they are read
+// or written once, and should not push table buckets out of L2).
+template <class T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream(uint8_t *p, uint8_t v) { __stcs(reinterpret_cast<signed char *>(p), (signed char)v); }
+__device__ __forceinline__ void st_stream(uint32_t *p, uint32_t v) { __stcs(reinterpret_cast<unsigned int *>(p), v); }
+__device__ __forceinline__ void st_stream(unsigned long long *p, unsigned long long v) { __stcs(p, v); }
+
+// ------------------------------------------------------------ group ops ---
+
+// A group is G consecutive lanes of a warp (G = 1, 2, 4 or 8).
+template <int G> struct Group {
+    unsigned mask;   // lanes of this group
+    int base;        // first lane of the group
+    int sub;         // this lane's index inside the group
+    __device__ __forceinline__ Group() {
+        const int lane = threadIdx.x & 31;
+        base = lane & ~(G - 1);
+        sub = lane & (G - 1);
+        mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+    }
+    // Bits [0, G) = pred of the group's lanes.
+    __device__ __forceinline__ unsigned ballot(bool pred) const {
+        if constexpr (G == 1) return pred ? 1u : 0u;
+        else return (__ballot_sync(mask, pred) >> base) & ((1u << G) - 1u);
+    }
+    template <class T> __device__ __forceinline__ T bcast(T v, int src_sub) const {
+        if constexpr (G == 1) return v;
+        else return __shfl_sync(mask, v, base + src_sub);
+    }
+};
+
+// Keys handled by a warp per tile: (32 / G) groups of KPT keys.
+template <int BB, int LB, int KPT> struct Shape {
+    static constexpr int G = BB / LB;
+    static constexpr int GROUPS = 32 / G;
+    static constexpr int TILE = GROUPS * KPT;
+};
+
+// Load the KPT keys of this group (tile position `first`), vectorised when the
+// whole run is inside [0, n) and aligned.
+template <int KPT, class K>
+__device__ __forceinline__ void load_keys(const K *keys, long long first, long long n, K (&k)[KPT], uint32_t &valid) {
+    valid = 0;
+    if constexpr (KPT * sizeof(K) >= 8) {
+        constexpr int VB = KPT * sizeof(K) >= 16 ? 16 : 8;
+        const bool vec = first + KPT <= n &&
+                         ((reinterpret_cast<uintptr_t>(keys + first) & (VB - 1)) == 0);
+        if (vec) {
+            if constexpr (VB == 16) {
+#pragma unroll
+                for (int q = 0; q < (int)(KPT * sizeof(K)) / 16; ++q) {
+                    uint4 u = __ldcs(reinterpret_cast<const uint4 *>(keys + first) + q);
+                    K tmp[16 / sizeof(K)];
+                    memcpy(tmp, &u, 16);
+#pragma unroll
+                    for (int e = 0; e < (int)(16 / sizeof(K)); ++e) k[q * (16 / sizeof(K)) + e] = tmp[e];
+                }
+            } else {
+                uint2 u = __ldcs(reinterpret_cast<const uint2 *>(keys + first));
+                memcpy(&k[0], &u, 8);
+            }
+            valid = (1u << KPT) - 1u;
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        if (first + j < n) {
+            k[j] = ld_stream(keys + first + j);
+            valid |= 1u << j;
+        } else {
+            k[j] = 0;
+        }
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ int side_index(typename Traits<KIND>::Key k) {
+    using T = Traits<KIND>;
+    return k == T::EMPTY ? 0 : (k == T::TOMB ? 1 : -1);
+}
+
+// Per-key results of a tile before they are written.
+template <int KPT> struct TileResult {
+    uint32_t st[KPT];
+    unsigned long long val[KPT];
+};
+
+// Duplicate folding inside a warp (__match_any_sync over the valid keys of
+// slot j of every group).  Returns the lane whose group leads key j, or -1
+// if this lane's group leads (or folding is off).  All 32 lanes must call it.
+template <int KIND, int G, int KPT>
+__device__ __forceinline__ void fold_duplicates(const typename Traits<KIND>::Key (&k)[KPT], uint32_t valid,
+                                                int (&leader)[KPT]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        const bool v = (valid >> j) & 1u;
+        const unsigned act = __ballot_sync(0xffffffffu, v);
+        leader[j] = -1;
+        if (v) {
+            const unsigned peers = __match_any_sync(act, k[j]);
+            const int first = __ffs(peers) - 1;
+            // lanes of the same group share a key, so the lowest peer lane is
+            // in the leading group; a lane leads if that lane is in its group
+            if ((first & ~(G - 1)) != (lane & ~(G - 1))) leader[j] = first;
+        }
+    }
+}
+
+// ---------------------------------------------------------- insert core ---
+
+template <int KIND, int BB, int LB, int KPT>
+__device__ __forceinline__ void insert_group(const View &v, const typename Traits<KIND>::Key (&k)[KPT],
+                                             const unsigned long long (&val)[KPT], uint32_t todo,
+                                             TileResult<KPT> &res, uint32_t &n_ins, uint32_t &n_new_slot) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    constexpr int G = BB / LB;
+    constexpr int SPL = LB / T::SLOT;   // slots per lane
+    const Group<G> grp;
+
+    unsigned long long b[KPT], b0[KPT], ffb[KPT];
+    uint32_t probes[KPT], restarts[KPT], ffs_slot[KPT];
+    bool ff_empty[KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        b0[j] = b[j] = (todo >> j & 1u) ? first_bucket(v, (unsigned long long)k[j]) : 0ull;
+        probes[j] = 0;
+        restarts[j] = 0;
+        ffb[j] = ~0ull;
+        ffs_slot[j] = 0;
+        ff_empty[j] = false;
+    }
+    uint32_t active = todo;
+    while (active) {
+        LaneWords<LB> lw[KPT];
+#pragma unroll
+        for (int j = 0; j < KPT; ++j)
+            if (active >> j & 1u) lw[j].load(v.slots + b[j] * BB + grp.sub * LB);
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            if (!(active >> j & 1u)) continue;
+            uint32_t lm = 0, le = 0, lt = 0;
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                const Key ks = slot_key<KIND, LB>(lw[j], s);
+                lm |= (uint32_t)(ks == k[j]) << s;
+                le |= (uint32_t)(ks == T::EMPTY) << s;
+                lt |= (uint32_t)(ks == T::TOMB) << s;
+            }
+            if (grp.ballot(lm != 0)) {           // already stored
+                res.st[j] = ST_EXISTS;
+                active &= ~(1u << j);
+                continue;
+            }
+            const unsigned ge = grp.ballot(le != 0);
+            if (ffb[j] == ~0ull) {               // remember the first free slot
+                const unsigned gf = grp.ballot((le | lt) != 0);
+                if (gf) {
+                    const int owner = __ffs(gf) - 1;
+                    const uint32_t lf = grp.bcast(le | lt, owner);
+                    const uint32_t lemp = grp.bcast(le, owner);
+                    const int s = __ffs(lf) - 1;
+                    ffb[j] = b[j];
+                    ffs_slot[j] = owner * SPL + s;
+                    ff_empty[j] = (lemp >> s) & 1u;
+                }
+            }
+            bool claim = ge != 0;
+            if (!claim) {
+                ++probes[j];
+                if (probes[j] >= v.nb) {
+                    if (ffb[j] == ~0ull) {       // no free slot anywhere
+                        res.st[j] = ST_OVERFLOW;
+                        active &= ~(1u << j);
+                        continue;
+                    }
+                    claim = true;                // only tombstones were free
+                } else {
+                    b[j] = next_bucket(v, b[j]);
+                    continue;
+                }
+            }
+            // claim the first free slot seen on this probe
+            const int owner = ffs_slot[j] / SPL;
+            const Key expect = ff_empty[j] ? T::EMPTY : T::TOMB;
+            Key old = expect;
+            if (grp.sub == owner) {
+                unsigned char *slot = v.slots + ffb[j] * BB + (size_t)ffs_slot[j] * T::SLOT;
+                old = cas_key<KIND>(slot, expect, k[j]);
+                if (old == expect) store_val<KIND>(slot, val[j]);
+            }
+            old = grp.bcast(old, owner);
+            if (old == expect) {
+                res.st[j] = ST_INSERTED;
+                if (grp.sub == 0) {
+                    ++n_ins;
+                    n_new_slot += ff_empty[j] ? 1u : 0u;
+                }
+                active &= ~(1u << j);
+            } else if (old == k[j]) {
+                res.st[j] = ST_EXISTS;           // an equal key won the race
+                active &= ~(1u << j);
+            } else if (++restarts[j] > kMaxRestarts) {
+                if (grp.sub == 0) atomicOr(&v.hdr->err, ERR_PROBE_BOUND);
+                res.st[j] = ST_OVERFLOW;
+                active &= ~(1u << j);
+            } else {                             // lost the slot to another key
+                b[j] = b0[j];
+                probes[j] = 0;
+                ffb[j] = ~0ull;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ find core ---
+
+template <int KIND, int BB, int LB, int KPT>
+__device__ __forceinline__ void find_group(const View &v, const typename Traits<KIND>::Key (&k)[KPT], uint32_t todo,
+                                           TileResult<KPT> &res) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    constexpr int G = BB / LB;
+    constexpr int SPL = LB / T::SLOT;
+    const Group<G> grp;
+
+    unsigned long long b[KPT];
+    uint32_t probes[KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        b[j] = (todo >> j & 1u) ? first_bucket(v, (unsigned long long)k[j]) : 0ull;
+        probes[j] = 0;
+    }
+    uint32_t active = todo;
+    while (active) {
+        LaneWords<LB> lw[KPT];
+#pragma unroll
+        for (int j = 0; j < KPT; ++j)
+            if (active >> j & 1u) lw[j].load(v.slots + b[j] * BB + grp.sub * LB);
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            if (!(active >> j & 1u)) continue;
+            uint32_t lm = 0, le = 0;
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                const Key ks = slot_key<KIND, LB>(lw[j], s);
+                lm |= (uint32_t)(ks == k[j]) << s;
+                le |= (uint32_t)(ks == T::EMPTY) << s;
+            }
+            const unsigned gm = grp.ballot(lm != 0);
+            if (gm) {
+                const int owner = __ffs(gm) - 1;
+                unsigned long long val = 0;
+                if constexpr (T::MAP) {
+                    if (grp.sub == owner) val = slot_val<KIND, LB>(lw[j], __ffs(lm) - 1);
+                    val = grp.bcast(val, owner);
+                }
+                res.st[j] = 1;
+                res.val[j] = val;
+                active &= ~(1u << j);
+            } else if (grp.ballot(le != 0) || ++probes[j] >= v.nb) {
+                res.st[j] = 0;
+                res.val[j] = 0;
+                active &= ~(1u << j);
+            } else {
+                b[j] = next_bucket(v, b[j]);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- erase core ---
+
+template <int KIND, int BB, int LB, int KPT>
+__device__ __forceinline__ void erase_group(const View &v, const typename Traits<KIND>::Key (&k)[KPT], uint32_t todo,
+                                            TileResult<KPT> &res, uint32_t &n_del) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    constexpr int G = BB / LB;
+    constexpr int SPL = LB / T::SLOT;
+    const Group<G> grp;
+
+    unsigned long long b[KPT];
+    uint32_t probes[KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        b[j] = (todo >> j & 1u) ? first_bucket(v, (unsigned long long)k[j]) : 0ull;
+        probes[j] = 0;
+    }
+    uint32_t active = todo;
+    while (active) {
+        LaneWords<LB> lw[KPT];
+#pragma unroll
+        for (int j = 0; j < KPT; ++j)
+            if (active >> j & 1u) lw[j].load(v.slots + b[j] * BB + grp.sub * LB);
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            if (!(active >> j & 1u)) continue;
+            uint32_t lm = 0, le = 0;
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                const Key ks = slot_key<KIND, LB>(lw[j], s);
+                lm |= (uint32_t)(ks == k[j]) << s;
+                le |= (uint32_t)(ks == T::EMPTY) << s;
+            }
+            const unsigned gm = grp.ballot(lm != 0);
+            if (gm) {
+                const int owner = __ffs(gm) - 1;
+                Key old = T::TOMB;
+                if (grp.sub == owner) {
+                    unsigned char *slot = v.slots + b[j] * BB + (size_t)(owner * SPL + __ffs(lm) - 1) * T::SLOT;
+                    old = cas_key<KIND>(slot, k[j], T::TOMB);
+                }
+                old = grp.bcast(old, owner);
+                // a failed swap means an equal key in this batch erased it first
+                res.st[j] = old == k[j] ? ST_ERASED : ST_NOT_FOUND;
+                if (old == k[j] && grp.sub == 0) ++n_del;
+                active &= ~(1u << j);
+            } else if (grp.ballot(le != 0) || ++probes[j] >= v.nb) {
+                res.st[j] = ST_NOT_FOUND;
+                active &= ~(1u << j);
+            } else {
+                b[j] = next_bucket(v, b[j]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ warp tiles ---
+// One warp processes keys [tile_base, tile_base + TILE) of a call.  These are
+// shared by the one-launch-per-call kernels and the batched persistent kernel.
+
+template <class V> __device__ __forceinline__ unsigned long long widen(V x) { return (unsigned long long)x; }
+
+template <int KIND, int BB, int LB, int KPT>
+__device__ __forceinline__ void insert_tile(const View &v, const typename Traits<KIND>::Key *keys,
+                                            const typename Traits<KIND>::Val *vals, long long n, uint8_t *status,
+                                            long long tile_base, bool fold) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    using S = Shape<BB, LB, KPT>;
+    const int lane = threadIdx.x & 31;
+    const long long first = tile_base + (long long)(lane / S::G) * KPT;
+    const bool lead_lane = (lane & (S::G - 1)) == 0;
+
+    Key k[KPT];
+    uint32_t valid;
+    load_keys<KPT>(keys, first, n, k, valid);
+    unsigned long long val[KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) val[j] = (T::MAP && (valid >> j & 1u)) ? widen(ld_stream(vals + first + j)) : 0ull;
+
+    int leader[KPT];
+    if (fold) fold_duplicates<KIND, S::G, KPT>(k, valid, leader);
+    else {
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) leader[j] = -1;
+    }
+
+    TileResult<KPT> res;
+    uint32_t todo = 0, n_ins = 0, n_new = 0;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        res.st[j] = ST_EXISTS;
+        if (!(valid >> j & 1u) || leader[j] >= 0) continue;
+        const int side = side_index<KIND>(k[j]);
+        if (side >= 0) {                         // key equal to a marker: side slot
+            uint32_t won = 0;
+            if (lead_lane) {
+                won = atomicCAS(&v.hdr->side_present[side], 0u, 1u) == 0u;
+                if (won) v.hdr->side_val[side] = val[j];
+                n_ins += won;
+            }
+            res.st[j] = Group<S::G>().bcast(won, 0) ? ST_INSERTED : ST_EXISTS;
+            continue;
+        }
+        todo |= 1u << j;
+    }
+    insert_group<KIND, BB, LB, KPT>(v, k, val, todo, res, n_ins, n_new);
+
+    if (fold) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            const uint32_t ls = __shfl_sync(0xffffffffu, res.st[j], leader[j] < 0 ? lane : leader[j]);
+            if (leader[j] >= 0) res.st[j] = ls == ST_OVERFLOW ? ST_OVERFLOW : ST_EXISTS;
+        }
+    }
+    uint32_t over = 0;
+    if (lead_lane) {
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            if (!(valid >> j & 1u)) continue;
+            over |= res.st[j] == ST_OVERFLOW;
+            if (status) st_stream(status + first + j, (uint8_t)res.st[j]);
+        }
+    }
+    __syncwarp();
+    const uint32_t w_ins = __reduce_add_sync(0xffffffffu, n_ins);
+    const uint32_t w_new = __reduce_add_sync(0xffffffffu, n_new);
+    const uint32_t w_over = __reduce_or_sync(0xffffffffu, over);
+    if (lane == 0) {
+        if (w_ins) atomicAdd(&v.hdr->live, (unsigned long long)w_ins);
+        if (w_new) atomicAdd(&v.hdr->used, (unsigned long long)w_new);
+        if (w_over) atomicOr(&v.hdr->err, ERR_OVERFLOW);
+    }
+}
+
+template <int KIND, int BB, int LB, int KPT>
+__device__ __forceinline__ void find_tile(const View &v, const typename Traits<KIND>::Key *keys, long long n,
+                                          uint8_t *found, typename Traits<KIND>::Val *vals_out, long long tile_base) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    using S = Shape<BB, LB, KPT>;
+    const int lane = threadIdx.x & 31;
+    const long long first = tile_base + (long long)(lane / S::G) * KPT;
+    const bool lead_lane = (lane & (S::G - 1)) == 0;
+
+    Key k[KPT];
+    uint32_t valid;
+    load_keys<KPT>(keys, first, n, k, valid);
+    TileResult<KPT> res;
+    uint32_t todo = 0;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        res.st[j] = 0;
+        res.val[j] = 0;
+        if (!(valid >> j & 1u)) continue;
+        const int side = side_index<KIND>(k[j]);
+        if (side >= 0) {
+            res.st[j] = *((volatile unsigned int *)&v.hdr->side_present[side]) ? 1u : 0u;
+            res.val[j] = res.st[j] ? *((volatile unsigned long long *)&v.hdr->side_val[side]) : 0ull;
+            continue;
+        }
+        todo |= 1u << j;
+    }
+    find_group<KIND, BB, LB, KPT>(v, k, todo, res);
+    if (lead_lane) {
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            if (!(valid >> j & 1u)) continue;
+            if (found) st_stream(found + first + j, (uint8_t)res.st[j]);
+            if constexpr (T::MAP) {
+                if (vals_out) st_stream(vals_out + first + j, (typename T::Val)res.val[j]);
+            }
+        }
+    }
+}
+
+template <int KIND, int BB, int LB, int KPT>
+__device__ __forceinline__ void erase_tile(const View &v, const typename Traits<KIND>::Key *keys, long long n,
+                                           uint8_t *status, long long tile_base, bool fold) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    using S = Shape<BB, LB, KPT>;
+    const int lane = threadIdx.x & 31;
+    const long long first = tile_base + (long long)(lane / S::G) * KPT;
+    const bool lead_lane = (lane & (S::G - 1)) == 0;
+
+    Key k[KPT];
+    uint32_t valid;
+    load_keys<KPT>(keys, first, n, k, valid);
+    int leader[KPT];
+    if (fold) fold_duplicates<KIND, S::G, KPT>(k, valid, leader);
+    else {
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) leader[j] = -1;
+    }
+    TileResult<KPT> res;
+    uint32_t todo = 0, n_del = 0;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        res.st[j] = ST_NOT_FOUND;
+        if (!(valid >> j & 1u) || leader[j] >= 0) continue;
+        const int side = side_index<KIND>(k[j]);
+        if (side >= 0) {
+            uint32_t won = 0;
+            if (lead_lane) {
+                won = atomicCAS(&v.hdr->side_present[side], 1u, 0u) == 1u;
+                n_del += won;
+            }
+            res.st[j] = Group<S::G>().bcast(won, 0) ? ST_ERASED : ST_NOT_FOUND;
+            continue;
+        }
+        todo |= 1u << j;
+    }
+    erase_group<KIND, BB, LB, KPT>(v, k, todo, res, n_del);
+    if (lead_lane && status) {
+#pragma unroll
+        for (int j = 0; j < KPT; ++j)
+            if (valid >> j & 1u) st_stream(status + first + j, (uint8_t)res.st[j]);
+    }
+    __syncwarp();
+    const uint32_t w_del = __reduce_add_sync(0xffffffffu, n_del);
+    if (lane == 0 && w_del) atomicAdd(&v.hdr->live, (unsigned long long)(-(long long)w_del));
+}
+
+}  // namespace hc

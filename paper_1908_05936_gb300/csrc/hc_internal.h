@@ -1,0 +1,40 @@
+// hc_internal.h -- declarations shared by the host API and the per-kind
+// kernel translation units.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hc {
+
+struct View;
+struct Header;
+
+enum : int { OP_INSERT = 0, OP_FIND = 1, OP_ERASE = 2 };
+
+struct LaunchShape {
+    int lane_bytes;       // 16 or 32
+    int keys_per_group;   // 1, 2, 4
+    int block;            // threads per block
+    int fold;             // 1 = fold equal keys inside a warp
+};
+
+#define HC_DECLARE_KIND(NAME)                                                                                       \
+    cudaError_t NAME##_range(int op, const View &v, int bb, const void *keys, const void *vals, long long n,        \
+                             uint8_t *out, void *vals_out, const LaunchShape &sh, cudaStream_t s);                  \
+    cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int sms,               \
+                             cudaStream_t s);                                                                       \
+    cudaError_t NAME##_dump(const View &v, unsigned long long phys, void *ko, void *vo, unsigned long long cap,     \
+                            int sms, cudaStream_t s);                                                               \
+    cudaError_t NAME##_rehash(const View &ov, unsigned long long ophys, const View &nv, int bb, int sms,            \
+                              cudaStream_t s);
+
+HC_DECLARE_KIND(set_u32)
+HC_DECLARE_KIND(set_u64)
+HC_DECLARE_KIND(map_i64_i32)
+HC_DECLARE_KIND(map_u64_u64)
+
+#undef HC_DECLARE_KIND
+
+}  // namespace hc

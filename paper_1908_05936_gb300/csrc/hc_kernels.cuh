@@ -1,0 +1,286 @@
+// hc_kernels.cuh -- the one-launch-per-call kernels (insert, find, erase,
+// clear, dump, rehash) and their launchers, instantiated once per container
+// kind by hc_kind_*.cu.
+#pragma once
+
+#include "hc_core.cuh"
+#include "hc_internal.h"
+
+namespace hc {
+
+// ------------------------------------------------------- range kernels ---
+
+template <int KIND, int BB, int LB, int KPT>
+__global__ void __launch_bounds__(512)
+k_insert(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
+         uint8_t *status, int fold) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    insert_tile<KIND, BB, LB, KPT>(v, keys, vals, n, status, warp * Shape<BB, LB, KPT>::TILE, fold != 0);
+}
+
+template <int KIND, int BB, int LB, int KPT>
+__global__ void __launch_bounds__(512)
+k_find(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *found,
+       typename Traits<KIND>::Val *vals_out) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    find_tile<KIND, BB, LB, KPT>(v, keys, n, found, vals_out, warp * Shape<BB, LB, KPT>::TILE);
+}
+
+template <int KIND, int BB, int LB, int KPT>
+__global__ void __launch_bounds__(512)
+k_erase(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status, int fold) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    erase_tile<KIND, BB, LB, KPT>(v, keys, n, status, warp * Shape<BB, LB, KPT>::TILE, fold != 0);
+}
+
+// ---------------------------------------------------------------- clear ---
+// Every slot EMPTY (all-ones bytes), then the slots past the capacity in the
+// last bucket become tombstones, and the header is zeroed.  32-byte stores.
+
+static __global__ void __launch_bounds__(256)
+k_fill_empty(unsigned char *slots, unsigned long long bytes, Header *hdr) {
+    const unsigned long long chunks = bytes / 32;
+    const unsigned long long ones = ~0ull;
+    for (unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
+         c += (unsigned long long)gridDim.x * blockDim.x) {
+        asm volatile("st.global.v4.u64 [%0], {%1,%1,%1,%1};" ::"l"(slots + c * 32), "l"(ones) : "memory");
+    }
+    if (blockIdx.x == 0 && threadIdx.x < sizeof(Header) / 8)
+        reinterpret_cast<unsigned long long *>(hdr)[threadIdx.x] = 0ull;
+}
+
+template <int KIND>
+__global__ void k_pad_tombstones(unsigned char *slots, unsigned long long first, unsigned long long count) {
+    using T = Traits<KIND>;
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) *reinterpret_cast<typename T::Key *>(slots + (first + i) * T::SLOT) = T::TOMB;
+}
+
+// ----------------------------------------------------------------- dump ---
+// Stored (key, value) pairs appended to the output through one atomic add per
+// warp on the header's cursor.
+
+template <int KIND>
+__global__ void __launch_bounds__(256)
+k_dump(View v, unsigned long long phys_slots, typename Traits<KIND>::Key *keys_out, typename Traits<KIND>::Val *vals_out,
+       unsigned long long cap) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    // iterate in whole-warp steps so every lane reaches the shuffles
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         base < phys_slots; base += stride) {
+        const unsigned long long i = base + lane;
+        Key key = T::EMPTY;
+        unsigned long long val = 0;
+        if (i < phys_slots) {
+            const unsigned char *slot = v.slots + i * T::SLOT;
+            key = *reinterpret_cast<const Key *>(slot);
+            if constexpr (T::MAP) {
+                if constexpr (sizeof(typename T::Val) == 4) val = *reinterpret_cast<const uint32_t *>(slot + 8);
+                else val = *reinterpret_cast<const unsigned long long *>(slot + 8);
+            }
+        }
+        const bool live = key != T::EMPTY && key != T::TOMB;
+        const unsigned m = __ballot_sync(0xffffffffu, live);
+        if (!m) continue;
+        unsigned long long pos0 = 0;
+        if (lane == 0) pos0 = atomicAdd(&v.hdr->dump_count, (unsigned long long)__popc(m));
+        pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+        if (live) {
+            const unsigned long long pos = pos0 + __popc(m & ((1u << lane) - 1u));
+            if (pos < cap) {
+                keys_out[pos] = key;
+                if constexpr (T::MAP) {
+                    if (vals_out) vals_out[pos] = (typename T::Val)val;
+                }
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 2) {
+        const int s = threadIdx.x;
+        if (v.hdr->side_present[s]) {
+            const unsigned long long pos = atomicAdd(&v.hdr->dump_count, 1ull);
+            if (pos < cap) {
+                keys_out[pos] = s == 0 ? T::EMPTY : T::TOMB;
+                if constexpr (T::MAP) {
+                    if (vals_out) vals_out[pos] = (typename T::Val)v.hdr->side_val[s];
+                }
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------- rehash ---
+// Each stored key of the old slot array goes to the first EMPTY slot of its
+// probe sequence in the new array (keys are distinct, so no equality test).
+
+template <int KIND, int BB>
+__global__ void __launch_bounds__(256)
+k_rehash(View old_v, unsigned long long old_phys, View new_v) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    constexpr int SPB = BB / T::SLOT;
+    uint32_t moved = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         base < old_phys; base += stride) {
+        const unsigned long long i = base + (threadIdx.x & 31);
+        if (i >= old_phys) continue;
+        const unsigned char *src = old_v.slots + i * T::SLOT;
+        const Key key = *reinterpret_cast<const Key *>(src);
+        if (key == T::EMPTY || key == T::TOMB) continue;
+        unsigned long long val = 0;
+        if constexpr (T::MAP) {
+            if constexpr (sizeof(typename T::Val) == 4) val = *reinterpret_cast<const uint32_t *>(src + 8);
+            else val = *reinterpret_cast<const unsigned long long *>(src + 8);
+        }
+        unsigned long long b = first_bucket(new_v, (unsigned long long)key);
+        bool done = false;
+        for (unsigned long long p = 0; p < new_v.nb && !done;) {
+            unsigned char *bucket = new_v.slots + b * BB;
+            int s = 0;
+            for (; s < SPB; ++s) {
+                Key ks;
+                if constexpr (sizeof(Key) == 4) ks = __ldcg(reinterpret_cast<const unsigned int *>(bucket + s * T::SLOT));
+                else ks = __ldcg(reinterpret_cast<const unsigned long long *>(bucket + s * T::SLOT));
+                if (ks == T::EMPTY) break;
+            }
+            if (s == SPB) {
+                b = next_bucket(new_v, b);
+                ++p;
+                continue;
+            }
+            if (cas_key<KIND>(bucket + s * T::SLOT, T::EMPTY, key) == T::EMPTY) {
+                store_val<KIND>(bucket + s * T::SLOT, val);
+                done = true;
+            }
+            // a lost race re-reads the same bucket
+        }
+        if (done) ++moved;
+        else atomicOr(&new_v.hdr->err, ERR_PROBE_BOUND);
+    }
+    const uint32_t w = __reduce_add_sync(0xffffffffu, moved);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&new_v.hdr->reinserted, (unsigned long long)w);
+}
+
+// ------------------------------------------------------------ launchers ---
+
+inline unsigned grid_for(long long n, int tile, int block) {
+    const long long warps = (n + tile - 1) / tile;
+    const long long threads = warps * 32;
+    return (unsigned)((threads + block - 1) / block);
+}
+
+template <int KIND, int BB, int LB, int KPT>
+cudaError_t launch_range_shape(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
+                               void *vals_out, int block, int fold, cudaStream_t s) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    using Val = typename T::Val;
+    constexpr int TILE = Shape<BB, LB, KPT>::TILE;
+    const unsigned grid = grid_for(n, TILE, block);
+    if (grid == 0) return cudaSuccess;
+    if (op == OP_INSERT)
+        k_insert<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, (const Val *)vals, n, out, fold);
+    else if (op == OP_FIND)
+        k_find<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, n, out, (Val *)vals_out);
+    else
+        k_erase<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, n, out, fold);
+    return cudaGetLastError();
+}
+
+template <int KIND, int BB, int LB>
+cudaError_t launch_range_kpt(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
+                             void *vals_out, const LaunchShape &sh, cudaStream_t s) {
+    switch (sh.keys_per_group) {
+        case 1: return launch_range_shape<KIND, BB, LB, 1>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, s);
+        case 2: return launch_range_shape<KIND, BB, LB, 2>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, s);
+        case 4: return launch_range_shape<KIND, BB, LB, 4>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int KIND, int BB>
+cudaError_t launch_range_lb(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
+                            void *vals_out, const LaunchShape &sh, cudaStream_t s) {
+    switch (sh.lane_bytes) {
+        case 16: return launch_range_kpt<KIND, BB, 16>(op, v, keys, vals, n, out, vals_out, sh, s);
+        case 32: return launch_range_kpt<KIND, BB, 32>(op, v, keys, vals, n, out, vals_out, sh, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int KIND>
+cudaError_t launch_range(int op, const View &v, int bucket_bytes, const void *keys, const void *vals, long long n,
+                         uint8_t *out, void *vals_out, const LaunchShape &sh, cudaStream_t s) {
+    switch (bucket_bytes) {
+        case 32: return launch_range_lb<KIND, 32>(op, v, keys, vals, n, out, vals_out, sh, s);
+        case 64: return launch_range_lb<KIND, 64>(op, v, keys, vals, n, out, vals_out, sh, s);
+        case 128: return launch_range_lb<KIND, 128>(op, v, keys, vals, n, out, vals_out, sh, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int KIND>
+cudaError_t launch_clear(const View &v, unsigned long long phys_slots, unsigned long long capacity, int sm_count,
+                         cudaStream_t s) {
+    const unsigned long long bytes = phys_slots * Traits<KIND>::SLOT;
+    const unsigned long long chunks = bytes / 32;
+    unsigned grid = (unsigned)std::min<unsigned long long>((chunks + 255) / 256, (unsigned long long)sm_count * 8);
+    if (grid == 0) grid = 1;
+    k_fill_empty<<<grid, 256, 0, s>>>(v.slots, bytes, v.hdr);
+    if (phys_slots > capacity) {
+        const unsigned long long pad = phys_slots - capacity;
+        k_pad_tombstones<KIND><<<(unsigned)((pad + 127) / 128), 128, 0, s>>>(v.slots, capacity, pad);
+    }
+    return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_dump(const View &v, unsigned long long phys_slots, void *keys_out, void *vals_out,
+                        unsigned long long cap, int sm_count, cudaStream_t s) {
+    using T = Traits<KIND>;
+    unsigned grid = (unsigned)std::min<unsigned long long>((phys_slots + 255) / 256, (unsigned long long)sm_count * 8);
+    if (grid == 0) grid = 1;
+    k_dump<KIND><<<grid, 256, 0, s>>>(v, phys_slots, (typename T::Key *)keys_out, (typename T::Val *)vals_out, cap);
+    return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_rehash(const View &old_v, unsigned long long old_phys, const View &new_v, int bucket_bytes,
+                          int sm_count, cudaStream_t s) {
+    unsigned grid = (unsigned)std::min<unsigned long long>((old_phys + 255) / 256, (unsigned long long)sm_count * 16);
+    if (grid == 0) grid = 1;
+    switch (bucket_bytes) {
+        case 32: k_rehash<KIND, 32><<<grid, 256, 0, s>>>(old_v, old_phys, new_v); break;
+        case 64: k_rehash<KIND, 64><<<grid, 256, 0, s>>>(old_v, old_phys, new_v); break;
+        case 128: k_rehash<KIND, 128><<<grid, 256, 0, s>>>(old_v, old_phys, new_v); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hc
+
+// Explicit per-kind entry points used by the host API.
+#define HC_INSTANTIATE_KIND(KIND, NAME)                                                                             \
+    namespace hc {                                                                                                  \
+    cudaError_t NAME##_range(int op, const View &v, int bb, const void *keys, const void *vals, long long n,        \
+                             uint8_t *out, void *vals_out, const LaunchShape &sh, cudaStream_t s) {                 \
+        return launch_range<KIND>(op, v, bb, keys, vals, n, out, vals_out, sh, s);                                  \
+    }                                                                                                               \
+    cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int sms,               \
+                             cudaStream_t s) {                                                                      \
+        return launch_clear<KIND>(v, phys, cap, sms, s);                                                            \
+    }                                                                                                               \
+    cudaError_t NAME##_dump(const View &v, unsigned long long phys, void *ko, void *vo, unsigned long long cap,     \
+                            int sms, cudaStream_t s) {                                                              \
+        return launch_dump<KIND>(v, phys, ko, vo, cap, sms, s);                                                     \
+    }                                                                                                               \
+    cudaError_t NAME##_rehash(const View &ov, unsigned long long ophys, const View &nv, int bb, int sms,            \
+                              cudaStream_t s) {                                                                     \
+        return launch_rehash<KIND>(ov, ophys, nv, bb, sms, s);                                                      \
+    }                                                                                                               \
+    }

@@ -1,0 +1,102 @@
+"""A GPU table and a CPU oracle table driven with the same calls."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import compare as C
+from oracle import oracle as O
+from paper_1908_05936_gb300.table import Table, to_device, to_numpy
+
+RESERVED = {
+    O.SET_U32: (np.uint32(0xFFFFFFFF), np.uint32(0xFFFFFFFE)),
+    O.SET_U64: (np.uint64(2**64 - 1), np.uint64(2**64 - 2)),
+    O.MAP_I64_I32: (np.int64(-1), np.int64(-2)),
+    O.MAP_U64_U64: (np.uint64(2**64 - 1), np.uint64(2**64 - 2)),
+}
+
+
+def random_keys(kind: int, n: int, rng: np.random.Generator, domain: np.ndarray | None = None) -> np.ndarray:
+    kdt = O.KEY_DTYPE[kind]
+    if domain is not None:
+        return domain[rng.integers(0, len(domain), size=n)]
+    bits = 32 if kind == O.SET_U32 else 64
+    raw = rng.integers(0, 2**bits, size=n, dtype=np.uint64 if bits == 64 else np.uint32)
+    return raw.view(kdt) if raw.dtype.itemsize == np.dtype(kdt).itemsize else raw.astype(kdt)
+
+
+def value_for(kind: int, keys: np.ndarray, rng: np.random.Generator | None = None) -> np.ndarray | None:
+    """Map values: random when rng is given (tests the keep-first rule), else
+    a fixed function of the key (deterministic contents under duplicates)."""
+    if kind not in O.VAL_DTYPE:
+        return None
+    n = len(keys)
+    if rng is not None:
+        if kind == O.MAP_I64_I32:
+            return rng.integers(-2**31, 2**31, size=n, dtype=np.int64).astype(np.int32)
+        return rng.integers(0, 2**64, size=n, dtype=np.uint64)
+    from workloads import splitmix
+    v = splitmix.value_of(keys)
+    if kind == O.MAP_I64_I32:
+        return (v % np.uint64(2**31)).astype(np.int32)
+    return v
+
+
+class Pair:
+    def __init__(self, kind: int, slots: int, bucket_bytes: int = 32, hash_mode: int = 0, seed: int = 0,
+                 shape: dict | None = None):
+        self.kind = kind
+        self.g = Table(kind, slots, bucket_bytes=bucket_bytes, hash_mode=hash_mode, seed=seed)
+        self.o = O.OracleTable(kind, slots)
+        if shape:
+            for op in (0, 1, 2):
+                self.g.set_launch(op, **shape)
+        self.is_map = self.g.is_map
+
+    def close(self):
+        self.g.close()
+        self.o.close()
+
+    def insert(self, keys, vals=None, check=True):
+        gs = self.g.insert(to_device(keys), to_device(vals) if self.is_map else None)
+        os_ = self.o.insert(keys, vals)
+        gs = to_numpy(gs, np.uint8)
+        if check:
+            C.assert_status(keys, gs, os_, "insert status")
+        return gs, os_
+
+    def find(self, keys):
+        gf, gv = self.g.find(to_device(keys))
+        of, ov = self.o.find(keys)
+        gf = to_numpy(gf, np.uint8)
+        gv = to_numpy(gv, O.VAL_DTYPE[self.kind]) if self.is_map else None
+        C.assert_find(gf, gv, of, ov)
+        return gf, gv
+
+    def erase(self, keys, check=True):
+        gs = to_numpy(self.g.erase(to_device(keys)), np.uint8)
+        os_ = self.o.erase(keys)
+        if check:
+            C.assert_status(keys, gs, os_, "erase status")
+        return gs, os_
+
+    def clear(self):
+        self.g.clear()
+        self.o.clear()
+
+    def rehash(self, s: int) -> bool:
+        ok_o = self.o.rehash(s)
+        try:
+            self.g.rehash(s)
+            ok_g = True
+        except Exception:
+            ok_g = False
+        assert ok_g == ok_o, f"rehash({s}) accepted by gpu={ok_g} oracle={ok_o}"
+        return ok_o
+
+    def check(self):
+        assert self.g.size() == self.o.size(), (self.g.size(), self.o.size())
+        gk, gv = self.g.dump_numpy()
+        ok, ov = self.o.dump()
+        C.assert_contents(gk, gv, ok, ov)
+        torch.cuda.synchronize()

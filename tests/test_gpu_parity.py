@@ -1,0 +1,256 @@
+"""GPU containers against the CPU oracle, through the C ABI (parity tests).
+
+Exact integer semantics: every comparison is bit-exact under the rules in
+compare.py (duplicate keys inside one batch compared as a multiset)."""
+import numpy as np
+import pytest
+import torch
+
+import compare as C
+from gpu_pair import RESERVED, Pair, random_keys, value_for
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+KINDS = (O.SET_U32, O.SET_U64, O.MAP_I64_I32, O.MAP_U64_U64)
+SHAPES = [  # (bucket bytes, lane bytes, keys per group, block, fold)
+    (32, 32, 1, 256, 1), (32, 16, 2, 128, 2), (32, 32, 4, 64, 1), (64, 32, 2, 256, 2), (64, 16, 4, 512, 1),
+    (128, 32, 1, 256, 1), (128, 16, 2, 96, 2), (128, 32, 4, 256, 1),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1908_05936_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield
+    torch.cuda.synchronize()
+
+
+def run_script(kind, slots, shape, seed, n_batches=30, domain_size=3000, max_batch=5000, rehash=True):
+    bb, lb, kpt, block, fold = shape
+    rng = np.random.default_rng(seed)
+    dom = np.concatenate([random_keys(kind, domain_size, rng), np.array(RESERVED[kind])])
+    p = Pair(kind, slots, bucket_bytes=bb, seed=seed,
+             shape=dict(lane_bytes=lb, keys_per_group=kpt, block=block, fold=fold))
+    try:
+        for b in range(n_batches):
+            op = rng.choice(["I", "I", "F", "E", "R", "C"] if rehash else ["I", "I", "F", "E"])
+            n = int(rng.integers(0, max_batch))
+            keys = random_keys(kind, n, rng, dom)
+            if op == "I":
+                p.insert(keys, value_for(kind, keys, rng))
+            elif op == "F":
+                p.find(keys)
+            elif op == "E":
+                p.erase(keys)
+            elif op == "R":
+                p.rehash(int(rng.integers(domain_size + 2, 2 * slots)))
+            elif op == "C" and rng.random() < 0.3:
+                p.clear()
+            if b % 7 == 0:
+                p.check()
+        p.check()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"bb{s[0]}-lb{s[1]}-k{s[2]}-b{s[3]}-f{s[4]}" for s in SHAPES])
+def test_random_scripts(kind, shape):
+    run_script(kind, 4096, shape, seed=hash((kind, shape)) % 1000)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_batch_sizes_and_duplicates(kind):
+    rng = np.random.default_rng(7)
+    p = Pair(kind, 1 << 14)
+    try:
+        for n in (0, 1, 31, 32, 33, 127, 128, 129, 4097):
+            keys = random_keys(kind, n, rng)
+            p.insert(keys, value_for(kind, keys, rng))
+            p.find(keys)
+        p.check()
+        # one key repeated across a whole batch: exactly one INSERTED
+        k = np.full(4097, random_keys(kind, 1, rng)[0])
+        gs, _ = p.insert(k, value_for(kind, k, rng))
+        assert (gs == C.INSERTED).sum() == 1 and (gs == C.EXISTS).sum() == 4096
+        gs, _ = p.erase(k)
+        assert (gs == C.ERASED).sum() == 1
+        # reserved bit patterns are ordinary keys
+        r = np.array(list(RESERVED[kind]) * 40, dtype=O.KEY_DTYPE[kind])
+        p.insert(r, value_for(kind, r, rng))
+        p.find(r)
+        p.check()
+        p.erase(r)
+        p.find(r)
+        p.check()
+        # keys not 16-byte aligned (scalar load path) and odd lengths
+        keys = random_keys(kind, 1001, rng)
+        dk = torch.from_numpy(keys.view(np.int32 if kind == O.SET_U32 else np.int64)).cuda()
+        st = p.g.insert(dk[1:], None if not p.is_map else torch.from_numpy(
+            value_for(kind, keys[1:]).view(np.int32 if kind == O.MAP_I64_I32 else np.int64)).cuda())
+        ost = p.o.insert(keys[1:], value_for(kind, keys[1:]))
+        C.assert_status(keys[1:], st.cpu().numpy(), ost)
+        p.find(keys)
+        p.check()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("bb", (32, 64, 128))
+@pytest.mark.parametrize("slots", (1, 3, 17, 64, 1000))
+def test_overflow_and_capacity(kind, bb, slots):
+    """Fill past the capacity: the only failure, reported per key and as a
+    sticky status; capacity is exact even when it is not a bucket multiple."""
+    rng = np.random.default_rng(slots + bb)
+    p = Pair(kind, slots, bucket_bytes=bb)
+    res = {int(x) for x in C.bits(np.array(RESERVED[kind]))}
+    try:
+        keys = np.concatenate([random_keys(kind, slots + 5, rng), np.array(RESERVED[kind])])
+        keys = np.concatenate([keys, keys[: len(keys) // 2]])          # duplicates too
+        rng.shuffle(keys)
+        vals = value_for(kind, keys)
+        gs, _ = p.insert(keys, vals, check=False)
+        gk, gv = p.g.dump_numpy()
+        C.check_overflow_insert(keys, gs, set(), slots, {int(x) for x in C.bits(gk)}, res)
+        assert p.g.size() == slots + 2
+        from paper_1908_05936_gb300 import _lib as L
+        assert p.g.status() == L.ERR_OVERFLOW
+        assert p.g.status() == L.OK
+        # stored values are the ones inserted with each stored key
+        if p.is_map:
+            f, v = p.g.find(torch.from_numpy(gk.view(np.int32 if kind == O.SET_U32 else np.int64)).cuda())
+            assert f.all()
+        # erase one stored key: exactly one more insert fits
+        victim = gk[:1]
+        assert p.g.erase(torch.from_numpy(victim.view(np.int64 if victim.dtype.itemsize == 8 else np.int32)).cuda()).cpu().numpy()[0] == C.ERASED
+        more = random_keys(kind, 3, rng)
+        st = p.g.insert(torch.from_numpy(more.view(np.int64 if more.dtype.itemsize == 8 else np.int32)).cuda(),
+                        None if not p.is_map else torch.from_numpy(value_for(kind, more).view(
+                            np.int32 if kind == O.MAP_I64_I32 else np.int64)).cuda()).cpu().numpy()
+        assert sorted(st.tolist()) == [C.INSERTED, C.OVERFLOW, C.OVERFLOW]
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_rehash_clear_and_reinsert(kind):
+    rng = np.random.default_rng(11)
+    p = Pair(kind, 2048, bucket_bytes=64)
+    try:
+        keys = random_keys(kind, 1500, rng)
+        p.insert(keys, value_for(kind, keys))
+        p.erase(keys[:700])
+        p.check()
+        live_regular = p.o.size_regular()
+        assert p.rehash(2048)               # same size: purges tombstones
+        st = p.g.stats()
+        assert st["used"] == live_regular and st["live"] == p.o.size()
+        assert p.rehash(4000)
+        assert not p.rehash(live_regular - 1)
+        assert p.rehash(live_regular)       # exactly full
+        p.check()
+        more = random_keys(kind, 10, rng)
+        gs, _ = p.insert(more, value_for(kind, more), check=False)
+        assert (gs == C.OVERFLOW).all()
+        p.rehash(5000)
+        p.insert(keys[:700], value_for(kind, keys[:700]))   # erase then re-insert
+        p.find(keys)
+        p.check()
+        p.clear()
+        p.check()
+        p.insert(keys, value_for(kind, keys))
+        p.check()
+    finally:
+        p.close()
+
+
+def test_set_u32_workload_full():
+    """set<u32>, 2^21 slots: insert 1M uniform keys, find 1M (half present),
+    erase 500k, all bit-exact against the oracle."""
+    from workloads import recipes
+    w = recipes.set_u32_workload()
+    p = Pair(O.SET_U32, w.slots)
+    try:
+        p.insert(w.insert_keys)
+        assert p.g.size() == len(np.unique(w.insert_keys))
+        p.find(w.find_keys)
+        p.erase(w.erase_keys)
+        p.find(w.find_keys)
+        p.check()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("bb,lb,kpt", [(32, 32, 2), (64, 32, 2), (32, 16, 4)])
+def test_map_u64_load_factor_sweep_scaled(bb, lb, kpt):
+    """map<u64,u64> at 2^20 slots: fill to 0.5/0.7/0.8/0.9 in batches, find
+    2^16 present and 2^16 absent keys at each step, erase 2^16, contents."""
+    from workloads import recipes
+    slots = 1 << 20
+    p = Pair(O.MAP_U64_U64, slots, bucket_bytes=bb,
+             shape=dict(lane_bytes=lb, keys_per_group=kpt))
+    try:
+        done = 0
+        for lf in (0.5, 0.7, 0.8, 0.9):
+            target = recipes.fill_count(slots, lf)
+            while done < target:
+                n = min(1 << 16, target - done)
+                k = recipes.map_fill_keys(done, n)
+                p.insert(k, value_for(O.MAP_U64_U64, k))
+                done += n
+            p.find(recipes.map_hit_keys(done, 1 << 16))
+            p.find(recipes.map_miss_keys(1 << 16, start=done))
+        p.erase(recipes.map_hit_keys(done, 1 << 16, salt=1))
+        p.find(recipes.map_hit_keys(done, 1 << 16))
+        p.check()
+    finally:
+        p.close()
+
+
+def test_teschner_hash_and_seeds_do_not_change_results():
+    """Results are independent of the hash function and its seed."""
+    rng = np.random.default_rng(3)
+    xyz = rng.integers(-50, 50, size=(20000, 3))
+    m = (1 << 21) - 1
+    keys = ((xyz[:, 0] & m) | ((xyz[:, 1] & m) << 21) | ((xyz[:, 2] & m) << 42)).astype(np.int64)
+    vals = value_for(O.MAP_I64_I32, keys)
+    outs = []
+    for hm, seed in ((0, 0), (0, 12345), (1, 0)):
+        p = Pair(O.MAP_I64_I32, 30011, hash_mode=hm, seed=seed)
+        try:
+            p.insert(keys[:15000], vals[:15000])
+            f, v = p.find(keys)
+            p.erase(keys[::3])
+            p.check()
+            outs.append((f, v))
+        finally:
+            p.close()
+    for f, v in outs[1:]:
+        assert np.array_equal(f, outs[0][0]) and np.array_equal(v, outs[0][1])
+
+
+@pytest.mark.parametrize("kind", (O.SET_U32, O.MAP_U64_U64))
+def test_host_buffer_calls(kind):
+    """hc_*_host: host arrays in, host results out, chunked staging (two
+    chunks here); same results as the oracle."""
+    rng = np.random.default_rng(5)
+    n = (1 << 22) + 12345
+    p = Pair(kind, 1 << 24)
+    try:
+        keys = random_keys(kind, n, rng)
+        vals = value_for(kind, keys)
+        st = p.g.insert_host(keys, vals)
+        C.assert_status(keys, st, p.o.insert(keys, vals))
+        q = np.concatenate([keys[: n // 2], random_keys(kind, n // 2, rng)])
+        f, v = p.g.find_host(q)
+        of, ov = p.o.find(q)
+        C.assert_find(f, v, of, ov)
+        st = p.g.erase_host(keys[::2])
+        C.assert_status(keys[::2], st, p.o.erase(keys[::2]))
+        p.check()
+    finally:
+        p.close()

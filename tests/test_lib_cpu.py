@@ -1,0 +1,68 @@
+"""libhc.so on the CPU: it loads, exports every entry point include/hc.h
+declares, and rejects bad arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1908_05936_gb300 import build
+    build.build()
+    from paper_1908_05936_gb300 import _lib
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hc.h")).read()
+    return sorted(set(re.findall(r"^HC_API\s+[\w\s\*]+?\b(hc_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1908_05936_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == names
+
+
+def test_abi_version(lib):
+    assert lib.hc_abi_version() == 1
+
+
+def test_argument_errors_before_any_launch(lib):
+    from paper_1908_05936_gb300 import _lib as L
+    h = ctypes.c_void_p()
+    assert lib.hc_create(None, 0, 16, None, None) == L.ERR_ARG
+    assert lib.hc_create(ctypes.byref(h), 9, 16, None, None) == L.ERR_ARG
+    assert b"kind" in lib.hc_last_error()
+    assert lib.hc_create(ctypes.byref(h), 0, 0, None, None) == L.ERR_ARG
+    bad = L.Config(48, 0, 0)
+    assert lib.hc_create(ctypes.byref(h), 0, 16, ctypes.byref(bad), None) == L.ERR_ARG
+    tes = L.Config(32, L.HASH_TESCHNER, 0)
+    assert lib.hc_create(ctypes.byref(h), L.SET_U64, 16, ctypes.byref(tes), None) == L.ERR_ARG
+    assert lib.hc_insert(None, None, None, 1, None, None) == L.ERR_ARG
+    assert lib.hc_find(None, None, 1, None, None, None) == L.ERR_ARG
+    assert lib.hc_erase(None, None, 1, None, None) == L.ERR_ARG
+    assert lib.hc_destroy(None) == L.OK
+    assert lib.hc_batch_create(None, None, 0, None, None) == L.ERR_ARG
+    assert lib.hc_batch_destroy(None) == L.OK
+
+
+def test_table_bytes(lib):
+    from paper_1908_05936_gb300 import _lib as L
+    b = ctypes.c_int64()
+    # header (256) + whole buckets of slots, rounded to 256 bytes
+    assert lib.hc_table_bytes(L.MAP_U64_U64, 1 << 28, None, ctypes.byref(b)) == L.OK
+    assert b.value == 256 + (1 << 28) * 16
+    assert lib.hc_table_bytes(L.SET_U32, 1, None, ctypes.byref(b)) == L.OK
+    assert b.value == 256 + 256          # one 32-byte bucket, rounded up
+    cfg = L.Config(128, 0, 0)
+    assert lib.hc_table_bytes(L.SET_U64, 17, ctypes.byref(cfg), ctypes.byref(b)) == L.OK
+    assert b.value == 256 + 256           # two 128-byte buckets
+    assert lib.hc_table_bytes(L.SET_U64, 0, None, ctypes.byref(b)) == L.ERR_ARG
