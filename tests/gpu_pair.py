@@ -25,20 +25,19 @@ def random_keys(kind: int, n: int, rng: np.random.Generator, domain: np.ndarray 
     return raw.view(kdt) if raw.dtype.itemsize == np.dtype(kdt).itemsize else raw.astype(kdt)
 
 
-def value_for(kind: int, keys: np.ndarray, rng: np.random.Generator | None = None) -> np.ndarray | None:
-    """Map values: random when rng is given (tests the keep-first rule), else
-    a fixed function of the key (deterministic contents under duplicates)."""
+def value_for(kind: int, keys: np.ndarray, salt: int = 0) -> np.ndarray | None:
+    """Map values as a fixed function of (key, salt): equal keys inside one
+    batch carry equal values, so the stored value does not depend on which
+    duplicate wins; a different salt per batch still exercises the rule that
+    inserting a present key keeps its old value."""
     if kind not in O.VAL_DTYPE:
         return None
-    n = len(keys)
-    if rng is not None:
-        if kind == O.MAP_I64_I32:
-            return rng.integers(-2**31, 2**31, size=n, dtype=np.int64).astype(np.int32)
-        return rng.integers(0, 2**64, size=n, dtype=np.uint64)
     from workloads import splitmix
-    v = splitmix.value_of(keys)
+    k = np.ascontiguousarray(keys)
+    k64 = k.view(np.uint32).astype(np.uint64) if k.dtype.itemsize == 4 else k.view(np.uint64)
+    v = splitmix.value_of(k64 ^ np.uint64(salt))
     if kind == O.MAP_I64_I32:
-        return (v % np.uint64(2**31)).astype(np.int32)
+        return (v & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.int32)
     return v
 
 
