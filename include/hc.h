@@ -92,21 +92,26 @@ enum { HC_OP_INSERT = 0, HC_OP_FIND = 1, HC_OP_ERASE = 2 };
  * The hash never changes a result, only where keys are stored. */
 enum { HC_HASH_MIX64 = 0, HC_HASH_TESCHNER = 1 };
 
-/* Layout chosen at creation.  Zero fields take the defaults. */
+/* Layout chosen at creation.  Zero fields take the defaults.  Keys live in an
+ * array of buckets; maps keep their values in a parallel array, so a probe
+ * reads keys only and a lookup that found its key reads one value. */
 typedef struct hc_config {
-    int32_t bucket_bytes;  /* 32, 64 or 128 (default 32): one probe reads one
-                              bucket; buckets are aligned to 32-byte sectors */
+    int32_t bucket_bytes;  /* bytes of keys per bucket: 32, 64 or 128
+                              (default 32); one probe reads one bucket;
+                              buckets are aligned to 32-byte sectors      */
     int32_t hash_mode;     /* HC_HASH_*; default HC_HASH_MIX64             */
     uint64_t seed;         /* hash seed (default 0)                        */
 } hc_config;
 
 /* Launch shape of one operation.  A group of bucket_bytes / lane_bytes
- * lanes probes a bucket together; each group handles keys_per_group keys at
- * once so that several bucket reads are in flight per lane.  Zero fields
- * keep the current value.  Results never depend on the shape. */
+ * lanes probes a bucket together (lane_bytes == bucket_bytes: one thread per
+ * key); each group handles keys_per_group keys at once so that several
+ * bucket reads are in flight per lane.  Zero fields keep the current value.
+ * Defaults: lane_bytes = bucket_bytes, keys_per_group 1, block 128, folding
+ * off.  Results never depend on the shape. */
 typedef struct hc_launch {
-    int32_t lane_bytes;       /* 16 or 32, at most bucket_bytes          */
-    int32_t keys_per_group;   /* 1, 2 or 4                               */
+    int32_t lane_bytes;       /* 32, 64 or 128, at most bucket_bytes     */
+    int32_t keys_per_group;   /* 1 or 2                                  */
     int32_t block;            /* threads per block: 64..512, multiple of 32  */
     int32_t fold_duplicates;  /* 1: equal keys inside a warp are folded to
                                  one probe (__match_any_sync); 2: off      */
@@ -118,7 +123,7 @@ typedef struct hc_stats_t {
     int64_t used;            /* slots not EMPTY: stored keys + tombstones,
                                 excluding the two side slots                  */
     int64_t capacity;        /* slots, as requested at create / rehash       */
-    int64_t slot_bytes;      /* bytes per slot                               */
+    int64_t slot_bytes;      /* bytes per slot: key plus value                */
     int64_t table_bytes;     /* device bytes held by the table               */
     uint32_t error_bits;     /* 1 = an insert overflowed, 2 = probe bound hit */
     uint32_t reserved;
@@ -157,6 +162,15 @@ HC_API hc_rc hc_get_launch(const hc_table *t, int32_t op, hc_launch *shape);
  * specified.  An overflow also sets the table's sticky error bit. */
 HC_API hc_rc hc_insert(hc_table *t, const void *d_keys, const void *d_vals, int64_t n,
                 uint8_t *d_status, void *stream);
+
+/* The insert half of a find-then-insert over a stream of candidate keys
+ * (the pattern of the Section 4.1 examples, which add only blocks that are
+ * not stored yet): d_found[i] is the flag hc_find wrote for the same
+ * d_keys[i], with no call on this table in between.  Keys whose flag is set
+ * get HC_EXISTS without a probe; the others are inserted exactly as by
+ * hc_insert.  Allocates nothing and needs no host synchronisation. */
+HC_API hc_rc hc_insert_if_absent(hc_table *t, const void *d_keys, const void *d_vals, const uint8_t *d_found,
+                                 int64_t n, uint8_t *d_status, void *stream);
 
 /* Range find / contains (Section 4.1): d_found[i] = 1 if d_keys[i] is
  * stored, else 0.  For maps, d_vals_out[i] (nullable: contains only)
@@ -231,7 +245,7 @@ typedef struct hc_batch_item {
 } hc_batch_item;
 
 typedef struct hc_batch_config {
-    int32_t lane_bytes;      /* as hc_launch; 0 = each table's own shape   */
+    int32_t lane_bytes;      /* 0: one thread per key (whole bucket); 32: 32-byte lanes */
     int32_t keys_per_group;
     int32_t block;           /* threads per block (0 = 256)                */
     int32_t blocks_per_sm;   /* persistent grid = SMs x this (0 = auto)    */

@@ -26,7 +26,7 @@ HASH_MIX64, HASH_TESCHNER = 0, 1
 
 EXPORTS = [
     "hc_abi_version", "hc_last_error", "hc_table_bytes", "hc_create", "hc_destroy", "hc_set_launch",
-    "hc_get_launch", "hc_insert", "hc_find", "hc_erase", "hc_insert_host", "hc_find_host", "hc_erase_host",
+    "hc_get_launch", "hc_insert", "hc_insert_if_absent", "hc_find", "hc_erase", "hc_insert_host", "hc_find_host", "hc_erase_host",
     "hc_size", "hc_stats", "hc_status", "hc_clear", "hc_rehash", "hc_dump", "hc_batch_create",
     "hc_batch_launch", "hc_batch_destroy",
 ]
@@ -80,6 +80,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_set_launch": (i32, [vp, i32, P(Launch)]),
         "hc_get_launch": (i32, [vp, i32, P(Launch)]),
         "hc_insert": (i32, [vp, vp, vp, i64, vp, vp]),
+        "hc_insert_if_absent": (i32, [vp, vp, vp, vp, i64, vp, vp]),
         "hc_find": (i32, [vp, vp, i64, vp, vp, vp]),
         "hc_erase": (i32, [vp, vp, i64, vp, vp]),
         "hc_insert_host": (i32, [vp, vp, vp, i64, vp, vp]),

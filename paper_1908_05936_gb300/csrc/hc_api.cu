@@ -37,17 +37,11 @@ hc_rc cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-int slot_bytes(int kind) {
-    switch (kind) {
-        case HC_SET_U32: return 4;
-        case HC_SET_U64: return 8;
-        case HC_MAP_I64_I32: return 16;
-        case HC_MAP_U64_U64: return 16;
-        default: return 0;
-    }
-}
+bool valid_kind(int kind) { return kind >= HC_SET_U32 && kind <= HC_MAP_U64_U64; }
 int key_bytes(int kind) { return kind == HC_SET_U32 ? 4 : 8; }
 int val_bytes(int kind) { return kind == HC_MAP_I64_I32 ? 4 : (kind == HC_MAP_U64_U64 ? 8 : 0); }
+// bytes a slot holds across the key and value arrays
+int slot_bytes(int kind) { return valid_kind(kind) ? key_bytes(kind) + val_bytes(kind) : 0; }
 bool is_map(int kind) { return kind == HC_MAP_I64_I32 || kind == HC_MAP_U64_U64; }
 
 int sm_count_of(int dev) {
@@ -80,27 +74,44 @@ hc_rc check_config(int kind, const hc_config *cfg, int *bb, int *hash_mode, unsi
     return HC_OK;
 }
 
+// Device memory of a table: [header 256 B][keys: phys slots][values: phys
+// slots (maps)], each part starting on a 256-byte boundary.
 struct Geometry {
-    long long nb, phys, bytes;
+    long long nb, phys, vals_off, bytes;
+    int pad_from;
 };
 
 Geometry geometry(int kind, long long slots, int bb) {
-    const long long spb = bb / slot_bytes(kind);
+    const long long spb = bb / key_bytes(kind);
     Geometry g;
     g.nb = (slots + spb - 1) / spb;
     g.phys = g.nb * spb;
-    g.bytes = (long long)sizeof(hc::Header) + g.phys * slot_bytes(kind);
-    g.bytes = (g.bytes + 255) / 256 * 256;
+    g.pad_from = (int)(spb - (g.phys - slots));
+    g.vals_off = (long long)sizeof(hc::Header) + (g.phys * key_bytes(kind) + 255) / 256 * 256;
+    g.bytes = g.vals_off + (g.phys * val_bytes(kind) + 255) / 256 * 256;
     return g;
 }
 
+hc::View make_view(void *mem, const Geometry &g, unsigned long long seed, int hash_mode, int kind) {
+    hc::View v;
+    v.hdr = static_cast<hc::Header *>(mem);
+    v.keys = static_cast<unsigned char *>(mem) + sizeof(hc::Header);
+    v.vals = val_bytes(kind) ? static_cast<unsigned char *>(mem) + g.vals_off : nullptr;
+    v.nb = g.nb;
+    v.seed = seed;
+    v.hash_mode = hash_mode;
+    v.pad_from = g.pad_from;
+    return v;
+}
+
 cudaError_t dispatch_range(int kind, int op, const hc::View &v, int bb, const void *keys, const void *vals, long long n,
-                           uint8_t *out, void *vals_out, const hc::LaunchShape &sh, cudaStream_t s) {
+                           uint8_t *out, void *vals_out, const hc::LaunchShape &sh, const uint8_t *skip,
+                           cudaStream_t s) {
     switch (kind) {
-        case HC_SET_U32: return hc::set_u32_range(op, v, bb, keys, vals, n, out, vals_out, sh, s);
-        case HC_SET_U64: return hc::set_u64_range(op, v, bb, keys, vals, n, out, vals_out, sh, s);
-        case HC_MAP_I64_I32: return hc::map_i64_i32_range(op, v, bb, keys, vals, n, out, vals_out, sh, s);
-        default: return hc::map_u64_u64_range(op, v, bb, keys, vals, n, out, vals_out, sh, s);
+        case HC_SET_U32: return hc::set_u32_range(op, v, bb, keys, vals, n, out, vals_out, sh, skip, s);
+        case HC_SET_U64: return hc::set_u64_range(op, v, bb, keys, vals, n, out, vals_out, sh, skip, s);
+        case HC_MAP_I64_I32: return hc::map_i64_i32_range(op, v, bb, keys, vals, n, out, vals_out, sh, skip, s);
+        default: return hc::map_u64_u64_range(op, v, bb, keys, vals, n, out, vals_out, sh, skip, s);
     }
 }
 
@@ -162,12 +173,12 @@ hc_rc range_checks(const hc_table *t, int op, const void *keys, const void *vals
 }
 
 hc_rc run_range(hc_table *t, int op, const void *keys, const void *vals, long long n, uint8_t *out, void *vals_out,
-                cudaStream_t s) {
+                cudaStream_t s, const uint8_t *skip = nullptr) {
     hc_rc rc = range_checks(t, op, keys, vals, n, out, vals_out);
     if (rc != HC_OK || n == 0) return rc;
     const hc::LaunchShape &sh = t->shape[op];
     cudaError_t e = dispatch_range(t->kind, op, t->view, t->bucket_bytes, keys, is_map(t->kind) ? vals : nullptr, n,
-                                   out, is_map(t->kind) ? vals_out : nullptr, sh, s);
+                                   out, is_map(t->kind) ? vals_out : nullptr, sh, skip, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the range kernel");
     return HC_OK;
 }
@@ -244,7 +255,7 @@ int32_t hc_abi_version(void) { return HC_ABI_VERSION; }
 const char *hc_last_error(void) { return g_last_error.c_str(); }
 
 hc_rc hc_table_bytes(int32_t kind, int64_t slots, const hc_config *cfg, int64_t *bytes) {
-    if (!slot_bytes(kind)) return fail(HC_ERR_ARG, "unknown kind %d", kind);
+    if (!valid_kind(kind)) return fail(HC_ERR_ARG, "unknown kind %d", kind);
     if (slots < 1) return fail(HC_ERR_ARG, "slots must be >= 1 (got %lld)", (long long)slots);
     if (!bytes) return fail(HC_ERR_ARG, "bytes is NULL");
     int bb, hm;
@@ -258,7 +269,7 @@ hc_rc hc_table_bytes(int32_t kind, int64_t slots, const hc_config *cfg, int64_t 
 hc_rc hc_create(hc_table **out, int32_t kind, int64_t slots, const hc_config *cfg, void *stream) {
     if (!out) return fail(HC_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (!slot_bytes(kind)) return fail(HC_ERR_ARG, "unknown kind %d", kind);
+    if (!valid_kind(kind)) return fail(HC_ERR_ARG, "unknown kind %d", kind);
     if (slots < 1) return fail(HC_ERR_ARG, "slots must be >= 1 (got %lld)", (long long)slots);
     int bb, hm;
     unsigned long long seed;
@@ -279,15 +290,10 @@ hc_rc hc_create(hc_table **out, int32_t kind, int64_t slots, const hc_config *cf
         delete t;
         return fail(HC_ERR_OOM, "cudaMalloc of %lld bytes failed: %s", (long long)g.bytes, cudaGetErrorString(e));
     }
-    t->view.hdr = static_cast<hc::Header *>(t->d_mem);
-    t->view.slots = static_cast<unsigned char *>(t->d_mem) + sizeof(hc::Header);
-    t->view.nb = g.nb;
-    t->view.seed = seed;
-    t->view.hash_mode = hm;
-    t->view.pad = 0;
-    const int lb = bb >= 32 ? 32 : 16;
-    for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{lb, 2, 256, 1};
-    t->shape[hc::OP_FIND].fold = 0;
+    t->view = make_view(t->d_mem, g, seed, hm, kind);
+    // one thread per key reading the whole bucket, one key in flight,
+    // 128-thread blocks: the best shape of the sweeps on GB300 for uniform keys
+    for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{bb, 1, 128, 0};
     e = dispatch_clear(t, t->view, t->phys, t->capacity, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         cudaFree(t->d_mem);
@@ -326,10 +332,10 @@ hc_rc hc_set_launch(hc_table *t, int32_t op, const hc_launch *shape) {
     if (shape->keys_per_group) sh.keys_per_group = shape->keys_per_group;
     if (shape->block) sh.block = shape->block;
     if (shape->fold_duplicates) sh.fold = shape->fold_duplicates == 1 ? 1 : 0;
-    if ((sh.lane_bytes != 16 && sh.lane_bytes != 32) || sh.lane_bytes > t->bucket_bytes)
-        return fail(HC_ERR_ARG, "lane_bytes must be 16 or 32 and at most the bucket size");
-    if (sh.keys_per_group != 1 && sh.keys_per_group != 2 && sh.keys_per_group != 4)
-        return fail(HC_ERR_ARG, "keys_per_group must be 1, 2 or 4");
+    if ((sh.lane_bytes != 32 && sh.lane_bytes != 64 && sh.lane_bytes != 128) || sh.lane_bytes > t->bucket_bytes)
+        return fail(HC_ERR_ARG, "lane_bytes must be 32, 64 or 128 and at most the bucket size");
+    if (sh.keys_per_group != 1 && sh.keys_per_group != 2)
+        return fail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
     if (sh.block < 64 || sh.block > 512 || sh.block % 32)
         return fail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 512]");
     t->shape[op] = sh;
@@ -350,6 +356,13 @@ hc_rc hc_get_launch(const hc_table *t, int32_t op, hc_launch *shape) {
 
 hc_rc hc_insert(hc_table *t, const void *d_keys, const void *d_vals, int64_t n, uint8_t *d_status, void *stream) {
     return run_range(t, hc::OP_INSERT, d_keys, d_vals, n, d_status, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+hc_rc hc_insert_if_absent(hc_table *t, const void *d_keys, const void *d_vals, const uint8_t *d_found, int64_t n,
+                          uint8_t *d_status, void *stream) {
+    if (n > 0 && !d_found) return fail(HC_ERR_ARG, "found flags array is NULL");
+    return run_range(t, hc::OP_INSERT, d_keys, d_vals, n, d_status, nullptr, static_cast<cudaStream_t>(stream),
+                     d_found);
 }
 
 hc_rc hc_find(hc_table *t, const void *d_keys, int64_t n, uint8_t *d_found, void *d_vals_out, void *stream) {
@@ -435,10 +448,7 @@ hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
         (void)cudaGetLastError();
         return fail(HC_ERR_OOM, "cudaMalloc of %lld bytes failed: %s", (long long)g.bytes, cudaGetErrorString(e));
     }
-    hc::View nv = t->view;
-    nv.hdr = static_cast<hc::Header *>(mem);
-    nv.slots = static_cast<unsigned char *>(mem) + sizeof(hc::Header);
-    nv.nb = g.nb;
+    hc::View nv = make_view(mem, g, t->view.seed, t->view.hash_mode, t->kind);
     e = dispatch_clear(t, nv, g.phys, new_slots, s);
     const int sms = sm_count_of(t->device);
     if (e == cudaSuccess) {

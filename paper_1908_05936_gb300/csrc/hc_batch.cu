@@ -60,7 +60,9 @@ __device__ __forceinline__ void run_chunk(const BatchItemDev &it, long long k0, 
     }
 }
 
-template <int KIND, int OP, int LB, int KPT>
+// WIDE: one thread per key reading the item's whole bucket; otherwise 32-byte
+// lanes (bucket_bytes / 32 lanes per key).
+template <int KIND, int OP, int WIDE, int KPT>
 __global__ void __launch_bounds__(256)
 k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_chunks, int tile,
               unsigned long long *counter) {
@@ -81,9 +83,9 @@ k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_c
         const long long k0 = ((long long)c - it.chunk_begin) * tile;
         const long long k1 = k0 + tile < it.n ? k0 + tile : it.n;
         switch (it.bb) {
-            case 32: run_chunk<KIND, OP, 32, LB, KPT>(it, k0, k1); break;
-            case 64: run_chunk<KIND, OP, 64, LB, KPT>(it, k0, k1); break;
-            default: run_chunk<KIND, OP, 128, LB, KPT>(it, k0, k1); break;
+            case 32: run_chunk<KIND, OP, 32, 32, KPT>(it, k0, k1); break;
+            case 64: run_chunk<KIND, OP, 64, WIDE ? 64 : 32, KPT>(it, k0, k1); break;
+            default: run_chunk<KIND, OP, 128, WIDE ? 128 : 32, KPT>(it, k0, k1); break;
         }
     }
 }
@@ -96,14 +98,8 @@ using PhaseKernel = void (*)(const BatchItemDev *, int, long long, int, unsigned
 
 template <int KIND, int OP>
 PhaseKernel pick_lb_kpt(int lb, int kpt) {
-    if (lb == 16) {
-        if (kpt == 1) return k_batch_phase<KIND, OP, 16, 1>;
-        if (kpt == 2) return k_batch_phase<KIND, OP, 16, 2>;
-        return k_batch_phase<KIND, OP, 16, 4>;
-    }
-    if (kpt == 1) return k_batch_phase<KIND, OP, 32, 1>;
-    if (kpt == 2) return k_batch_phase<KIND, OP, 32, 2>;
-    return k_batch_phase<KIND, OP, 32, 4>;
+    if (lb == 0) return kpt == 1 ? k_batch_phase<KIND, OP, 1, 1> : k_batch_phase<KIND, OP, 1, 2>;
+    return kpt == 1 ? k_batch_phase<KIND, OP, 0, 1> : k_batch_phase<KIND, OP, 0, 2>;
 }
 
 template <int KIND>
@@ -180,12 +176,12 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
     if (n_items < 0 || (n_items > 0 && !items)) return bfail(HC_ERR_ARG, "bad item list");
     hc_batch_config c{};
     if (cfg) c = *cfg;
-    const int lb = c.lane_bytes ? c.lane_bytes : 32;
-    const int kpt = c.keys_per_group ? c.keys_per_group : 2;
+    const int lb = c.lane_bytes;
+    const int kpt = c.keys_per_group ? c.keys_per_group : 1;
     const int block = c.block ? c.block : 256;
     const int tile = c.tile ? c.tile : 4096;
-    if (lb != 16 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 16 or 32");
-    if (kpt != 1 && kpt != 2 && kpt != 4) return bfail(HC_ERR_ARG, "keys_per_group must be 1, 2 or 4");
+    if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole bucket) or 32");
+    if (kpt != 1 && kpt != 2) return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
     if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
 
@@ -207,7 +203,6 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
                     return bfail(HC_ERR_ARG, "item keys NULL or misaligned");
                 if (op == HC_OP_INSERT && map && !it.d_vals) return bfail(HC_ERR_ARG, "insert item on a map without values");
                 if (op == HC_OP_FIND && !it.d_out) return bfail(HC_ERR_ARG, "find item without a found array");
-                if (lb > it.table->bucket_bytes) return bfail(HC_ERR_ARG, "lane_bytes exceeds an item's bucket size");
                 hc::BatchItemDev d{};
                 d.v = it.table->view;
                 d.keys = it.d_keys;

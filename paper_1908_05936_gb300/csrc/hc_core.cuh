@@ -1,34 +1,38 @@
 // hc_core.cuh -- device side of the GB300 hash containers.
 //
-// Layout.  A table is an array of nb buckets of BB bytes (32, 64 or 128),
-// each aligned to a 32-byte sector, holding BB / SLOT slots in
-// array-of-structures order:
-//   set<u32>       4-byte slot  = key
-//   set<u64>       8-byte slot  = key
-//   map<i64,i32>  16-byte slot  = key (8) | value (4) | padding (4)
-//   map<u64,u64>  16-byte slot  = key (8) | value (8)
-// A slot is EMPTY (all-ones key), a TOMBSTONE (all-ones minus one) or holds a
-// key.  The two keys whose bit patterns equal those markers live in two side
-// slots of the header instead (every bit pattern is a valid key: the paper
-// avoids placeholder keys, Section 5.1).  Slots past the requested capacity in
-// the last bucket are written as tombstones at clear time, so a table never
-// stores more than `capacity` keys in slots (fixed capacity, Section 4).
+// Layout.  A table holds `phys` slots in nb buckets of BB bytes of keys
+// (BB = 32, 64 or 128: one, two or four 32-byte sectors), followed, for maps,
+// by a parallel value array (structure of arrays):
+//   keys[phys]   uint32 (set<u32>) or 64-bit key bit patterns (other kinds)
+//   vals[phys]   int32 (map<i64,i32>) or uint64 (map<u64,u64>)
+// A probe reads key buckets only; a map reads one value when it has found
+// its key.  A key slot is EMPTY (all ones), a TOMBSTONE (all ones minus one)
+// or holds a key.  The two keys whose bit patterns equal those markers live
+// in two side slots of the header (every bit pattern is a valid key: the
+// paper avoids placeholder keys, Section 5.1).  Slots past the requested
+// capacity in the last bucket are padding: they hold TOMBSTONE and inserts
+// never claim them, so a table stores at most `capacity` keys in slots (fixed
+// capacity, Section 4).
 //
 // Probing.  A key hashes to a first bucket; buckets are visited in order,
 // wrapping around, at most nb of them.  A group of G = BB / LB lanes reads one
-// bucket together (each lane LB = 16 or 32 bytes, one vector load) and
-// combines its findings with __ballot_sync.  Each group works on KPT keys at
-// once: the bucket loads for all of them are issued before any is examined, so
-// a lane keeps several independent sector reads in flight.
+// bucket together (each lane LB = 32, 64 or 128 bytes with 32-byte vector
+// loads; G = 1 is one thread per key) and combines its findings with
+// __ballot_sync.  Each group may work on KPT keys at once, issuing all their
+// bucket loads before examining any.
 //
 //   insert: stop at the key (EXISTS) or at the first bucket holding an EMPTY
-//           slot; claim the first free slot (EMPTY or TOMBSTONE) seen on the
-//           way with a compare-and-swap of the key; a lost race restarts the
-//           probe from the first bucket.  A full table (no free slot in nb
-//           buckets) gives OVERFLOW, the only failure (Section 4).
-//   find:   stop at the key or at a bucket holding an EMPTY slot; take no lock
+//           slot; claim the first free slot (EMPTY or TOMBSTONE, not padding)
+//           seen on the way with a compare-and-swap of the key, then store
+//           the value; a lost race restarts the probe.  No free slot in nb
+//           buckets gives OVERFLOW, the only failure (Section 4).
+//   find:   stop at the key or at a bucket holding an EMPTY slot; no lock
 //           (lookups are non-blocking, Section 4).
 //   erase:  find, then swap the key for a TOMBSTONE with a compare-and-swap.
+// Slots go EMPTY -> key and TOMBSTONE -> key during inserts and key ->
+// TOMBSTONE during erases, never back to EMPTY (until clear or rehash); this
+// is the invariant that lets a lookup stop at the first bucket holding EMPTY
+// and lets equal keys racing in one insert batch end in one slot.
 //
 // Counters.  The header's live / used counters move by one atomic add per
 // warp (__reduce_add_sync of the lanes' counts).
@@ -45,14 +49,14 @@ enum : uint32_t { ERR_OVERFLOW = 1u, ERR_PROBE_BOUND = 2u };
 enum : int { HASH_MIX64 = 0, HASH_TESCHNER = 1 };
 
 // Restarts of an insert probe after lost compare-and-swap races.  Each lost
-// race means another key took a slot, so this bound is never reached by a
-// correct table; it only keeps every loop finite.
+// race means another key took a slot, so a correct table never reaches this
+// bound; it only keeps every loop finite.
 constexpr uint32_t kMaxRestarts = 1u << 16;
 
-// Device-resident table header (256 bytes, sits in front of the slots).
+// Device-resident table header (256 bytes, in front of the key array).
 struct alignas(256) Header {
     unsigned long long live;             // stored keys, side slots included
-    unsigned long long used;             // slots that are not EMPTY (keys + tombstones)
+    unsigned long long used;             // slots that are not EMPTY (keys + tombstones), padding excluded
     unsigned int err;                    // sticky ERR_* bits
     unsigned int side_present[2];        // [0]: all-ones key, [1]: all-ones-minus-one key
     unsigned int pad0;
@@ -65,40 +69,37 @@ static_assert(sizeof(Header) == 256, "header is one 256-byte block");
 // What a kernel needs to reach a table; passed by value (Section 3.7: a
 // shallow copy of a device object can be handed to kernels).
 struct View {
-    unsigned char *slots;
+    unsigned char *keys;         // nb * BB bytes
+    unsigned char *vals;         // phys values (maps), else null
     Header *hdr;
     unsigned long long nb;       // buckets
     unsigned long long seed;
     int hash_mode;
-    int pad;
+    int pad_from;                // slots at positions >= pad_from of the last bucket are padding
 };
 
 template <int KIND> struct Traits;
 template <> struct Traits<KIND_SET_U32> {
     using Key = uint32_t;
     using Val = uint32_t;
-    static constexpr int SLOT = 4;
     static constexpr bool MAP = false;
     static constexpr Key EMPTY = 0xFFFFFFFFu, TOMB = 0xFFFFFFFEu;
 };
 template <> struct Traits<KIND_SET_U64> {
     using Key = unsigned long long;
     using Val = unsigned long long;
-    static constexpr int SLOT = 8;
     static constexpr bool MAP = false;
     static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
 };
 template <> struct Traits<KIND_MAP_I64_I32> {
     using Key = unsigned long long;   // int64 keys are handled as bit patterns
     using Val = uint32_t;             // int32 values likewise
-    static constexpr int SLOT = 16;
     static constexpr bool MAP = true;
     static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
 };
 template <> struct Traits<KIND_MAP_U64_U64> {
     using Key = unsigned long long;
     using Val = unsigned long long;
-    static constexpr int SLOT = 16;
     static constexpr bool MAP = true;
     static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
 };
@@ -140,48 +141,29 @@ __device__ __forceinline__ unsigned long long next_bucket(const View &v, unsigne
 
 // --------------------------------------------------------------- memory ---
 
-// One lane's share of a bucket, LB bytes read with a single vector load that
-// is cached in L2 only (the slots are shared by all SMs and modified by
-// atomics; an L1 copy could be stale after a lost compare-and-swap).
-template <int LB> struct LaneWords;
-template <> struct LaneWords<16> {
-    unsigned long long w[2];
+// One lane's share of a bucket: LB bytes in 32-byte vector loads cached in L2
+// only (the slots are shared by all SMs and modified by atomics; an L1 copy
+// could be stale after a lost compare-and-swap).
+template <int LB> struct LaneWords {
+    static_assert(LB == 32 || LB == 64 || LB == 128, "lane bytes");
+    unsigned long long w[LB / 8];
     __device__ __forceinline__ void load(const unsigned char *p) {
-        asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(p));
-    }
-};
-template <> struct LaneWords<32> {
-    unsigned long long w[4];
-    __device__ __forceinline__ void load(const unsigned char *p) {
-        asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
-                     : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
+#pragma unroll
+        for (int q = 0; q < LB / 32; ++q)
+            asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(w[4 * q]), "=l"(w[4 * q + 1]), "=l"(w[4 * q + 2]), "=l"(w[4 * q + 3])
+                         : "l"(p + 32 * q));
     }
 };
 
 template <int KIND, int LB>
 __device__ __forceinline__ typename Traits<KIND>::Key slot_key(const LaneWords<LB> &lw, int s) {
-    using T = Traits<KIND>;
-    if constexpr (T::SLOT == 4) {
-        return (typename T::Key)(lw.w[s >> 1] >> ((s & 1) * 32));
-    } else if constexpr (T::SLOT == 8) {
-        return lw.w[s];
-    } else {
-        return lw.w[2 * s];
-    }
+    using Key = typename Traits<KIND>::Key;
+    if constexpr (sizeof(Key) == 4) return (Key)(lw.w[s >> 1] >> ((s & 1) * 32));
+    else return lw.w[s];
 }
 
-template <int KIND, int LB>
-__device__ __forceinline__ unsigned long long slot_val(const LaneWords<LB> &lw, int s) {
-    using T = Traits<KIND>;
-    if constexpr (T::MAP) {
-        if constexpr (sizeof(typename T::Val) == 4) return (uint32_t)lw.w[2 * s + 1];
-        else return lw.w[2 * s + 1];
-    } else {
-        return 0ull;
-    }
-}
-
-// 32- or 64-bit compare-and-swap on a slot's key.
+// 32- or 64-bit compare-and-swap on a key slot.
 template <int KIND>
 __device__ __forceinline__ typename Traits<KIND>::Key cas_key(unsigned char *slot, typename Traits<KIND>::Key expect,
                                                              typename Traits<KIND>::Key desired) {
@@ -192,12 +174,16 @@ __device__ __forceinline__ typename Traits<KIND>::Key cas_key(unsigned char *slo
 }
 
 template <int KIND>
-__device__ __forceinline__ void store_val(unsigned char *slot, unsigned long long val) {
+__device__ __forceinline__ void store_val(const View &v, unsigned long long idx, unsigned long long val) {
     using T = Traits<KIND>;
-    if constexpr (T::MAP) {
-        if constexpr (sizeof(typename T::Val) == 4) *reinterpret_cast<uint32_t *>(slot + 8) = (uint32_t)val;
-        else *reinterpret_cast<unsigned long long *>(slot + 8) = val;
-    }
+    if constexpr (T::MAP) reinterpret_cast<typename T::Val *>(v.vals)[idx] = (typename T::Val)val;
+}
+
+template <int KIND>
+__device__ __forceinline__ unsigned long long load_val(const View &v, unsigned long long idx) {
+    using T = Traits<KIND>;
+    if constexpr (T::MAP) return (unsigned long long)__ldcg(reinterpret_cast<const typename T::Val *>(v.vals) + idx);
+    else return 0ull;
 }
 
 // Streaming loads/stores of the caller's arrays (evict-first: they are read
@@ -209,7 +195,7 @@ __device__ __forceinline__ void st_stream(unsigned long long *p, unsigned long l
 
 // ------------------------------------------------------------ group ops ---
 
-// A group is G consecutive lanes of a warp (G = 1, 2, 4 or 8).
+// A group is G consecutive lanes of a warp (G = 1, 2 or 4).
 template <int G> struct Group {
     unsigned mask;   // lanes of this group
     int base;        // first lane of the group
@@ -218,7 +204,7 @@ template <int G> struct Group {
         const int lane = threadIdx.x & 31;
         base = lane & ~(G - 1);
         sub = lane & (G - 1);
-        mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+        mask = ((1u << G) - 1u) << base;
     }
     // Bits [0, G) = pred of the group's lanes.
     __device__ __forceinline__ unsigned ballot(bool pred) const {
@@ -236,6 +222,15 @@ template <int BB, int LB, int KPT> struct Shape {
     static constexpr int G = BB / LB;
     static constexpr int GROUPS = 32 / G;
     static constexpr int TILE = GROUPS * KPT;
+};
+
+// Slot-layout constants of a (kind, bucket, lane) combination.
+template <int KIND, int BB, int LB> struct Layout {
+    static constexpr int KB = (int)sizeof(typename Traits<KIND>::Key);
+    static constexpr int SPL = LB / KB;   // key slots per lane (<= 32)
+    static constexpr int SPB = BB / KB;   // key slots per bucket
+    static constexpr uint32_t ALL = SPL == 32 ? 0xffffffffu : ((1u << SPL) - 1u);
+    static_assert(SPL <= 32, "lane masks are 32 bits");
 };
 
 // Load the KPT keys of this group (tile position `first`), vectorised when the
@@ -289,8 +284,8 @@ template <int KPT> struct TileResult {
 };
 
 // Duplicate folding inside a warp (__match_any_sync over the valid keys of
-// slot j of every group).  Returns the lane whose group leads key j, or -1
-// if this lane's group leads (or folding is off).  All 32 lanes must call it.
+// slot j of every group).  leader[j] = the lane whose group leads key j, or -1
+// if this lane's group leads.  All 32 lanes must call it.
 template <int KIND, int G, int KPT>
 __device__ __forceinline__ void fold_duplicates(const typename Traits<KIND>::Key (&k)[KPT], uint32_t valid,
                                                 int (&leader)[KPT]) {
@@ -303,11 +298,22 @@ __device__ __forceinline__ void fold_duplicates(const typename Traits<KIND>::Key
         if (v) {
             const unsigned peers = __match_any_sync(act, k[j]);
             const int first = __ffs(peers) - 1;
-            // lanes of the same group share a key, so the lowest peer lane is
-            // in the leading group; a lane leads if that lane is in its group
+            // lanes of one group share a key, so the lowest peer lane is in
+            // the leading group; a lane leads if that lane is in its group
             if ((first & ~(G - 1)) != (lane & ~(G - 1))) leader[j] = first;
         }
     }
+}
+
+// Slots of this lane that are not padding in bucket b (padding exists only in
+// the last bucket).
+template <int KIND, int BB, int LB>
+__device__ __forceinline__ uint32_t claimable(const View &v, unsigned long long b, int sub) {
+    using Lay = Layout<KIND, BB, LB>;
+    if (b != v.nb - 1) return Lay::ALL;
+    const int lim = v.pad_from - sub * Lay::SPL;
+    if (lim >= Lay::SPL) return Lay::ALL;
+    return lim <= 0 ? 0u : ((1u << lim) - 1u);
 }
 
 // ---------------------------------------------------------- insert core ---
@@ -318,8 +324,9 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
                                              TileResult<KPT> &res, uint32_t &n_ins, uint32_t &n_new_slot) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
+    using Lay = Layout<KIND, BB, LB>;
     constexpr int G = BB / LB;
-    constexpr int SPL = LB / T::SLOT;   // slots per lane
+    constexpr int SPL = Lay::SPL;
     const Group<G> grp;
 
     unsigned long long b[KPT], b0[KPT], ffb[KPT];
@@ -339,7 +346,7 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.slots + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(v.keys + b[j] * BB + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;
@@ -358,6 +365,7 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
             }
             const unsigned ge = grp.ballot(le != 0);
             if (ffb[j] == ~0ull) {               // remember the first free slot
+                lt &= claimable<KIND, BB, LB>(v, b[j], grp.sub);
                 const unsigned gf = grp.ballot((le | lt) != 0);
                 if (gf) {
                     const int owner = __ffs(gf) - 1;
@@ -389,9 +397,9 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
             const Key expect = ff_empty[j] ? T::EMPTY : T::TOMB;
             Key old = expect;
             if (grp.sub == owner) {
-                unsigned char *slot = v.slots + ffb[j] * BB + (size_t)ffs_slot[j] * T::SLOT;
-                old = cas_key<KIND>(slot, expect, k[j]);
-                if (old == expect) store_val<KIND>(slot, val[j]);
+                const unsigned long long idx = ffb[j] * Lay::SPB + ffs_slot[j];
+                old = cas_key<KIND>(v.keys + idx * Lay::KB, expect, k[j]);
+                if (old == expect) store_val<KIND>(v, idx, val[j]);
             }
             old = grp.bcast(old, owner);
             if (old == expect) {
@@ -424,8 +432,9 @@ __device__ __forceinline__ void find_group(const View &v, const typename Traits<
                                            TileResult<KPT> &res) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
+    using Lay = Layout<KIND, BB, LB>;
     constexpr int G = BB / LB;
-    constexpr int SPL = LB / T::SLOT;
+    constexpr int SPL = Lay::SPL;
     const Group<G> grp;
 
     unsigned long long b[KPT];
@@ -440,7 +449,7 @@ __device__ __forceinline__ void find_group(const View &v, const typename Traits<
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.slots + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(v.keys + b[j] * BB + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;
@@ -456,7 +465,7 @@ __device__ __forceinline__ void find_group(const View &v, const typename Traits<
                 const int owner = __ffs(gm) - 1;
                 unsigned long long val = 0;
                 if constexpr (T::MAP) {
-                    if (grp.sub == owner) val = slot_val<KIND, LB>(lw[j], __ffs(lm) - 1);
+                    if (grp.sub == owner) val = load_val<KIND>(v, b[j] * Lay::SPB + owner * SPL + (__ffs(lm) - 1));
                     val = grp.bcast(val, owner);
                 }
                 res.st[j] = 1;
@@ -480,8 +489,9 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
                                             TileResult<KPT> &res, uint32_t &n_del) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
+    using Lay = Layout<KIND, BB, LB>;
     constexpr int G = BB / LB;
-    constexpr int SPL = LB / T::SLOT;
+    constexpr int SPL = Lay::SPL;
     const Group<G> grp;
 
     unsigned long long b[KPT];
@@ -496,7 +506,7 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.slots + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(v.keys + b[j] * BB + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;
@@ -512,8 +522,8 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
                 const int owner = __ffs(gm) - 1;
                 Key old = T::TOMB;
                 if (grp.sub == owner) {
-                    unsigned char *slot = v.slots + b[j] * BB + (size_t)(owner * SPL + __ffs(lm) - 1) * T::SLOT;
-                    old = cas_key<KIND>(slot, k[j], T::TOMB);
+                    const unsigned long long idx = b[j] * Lay::SPB + owner * SPL + (__ffs(lm) - 1);
+                    old = cas_key<KIND>(v.keys + idx * Lay::KB, k[j], T::TOMB);
                 }
                 old = grp.bcast(old, owner);
                 // a failed swap means an equal key in this batch erased it first
@@ -539,7 +549,7 @@ template <class V> __device__ __forceinline__ unsigned long long widen(V x) { re
 template <int KIND, int BB, int LB, int KPT>
 __device__ __forceinline__ void insert_tile(const View &v, const typename Traits<KIND>::Key *keys,
                                             const typename Traits<KIND>::Val *vals, long long n, uint8_t *status,
-                                            long long tile_base, bool fold) {
+                                            long long tile_base, bool fold, const uint8_t *skip = nullptr) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using S = Shape<BB, LB, KPT>;
@@ -550,9 +560,17 @@ __device__ __forceinline__ void insert_tile(const View &v, const typename Traits
     Key k[KPT];
     uint32_t valid;
     load_keys<KPT>(keys, first, n, k, valid);
+    // keys a preceding find reported as stored are EXISTS without a probe
+    uint32_t present = 0;
+    if (skip) {
+#pragma unroll
+        for (int j = 0; j < KPT; ++j)
+            if ((valid >> j & 1u) && ld_stream(skip + first + j)) present |= 1u << j;
+    }
     unsigned long long val[KPT];
 #pragma unroll
-    for (int j = 0; j < KPT; ++j) val[j] = (T::MAP && (valid >> j & 1u)) ? widen(ld_stream(vals + first + j)) : 0ull;
+    for (int j = 0; j < KPT; ++j)
+        val[j] = (T::MAP && (valid >> j & 1u) && !(present >> j & 1u)) ? widen(ld_stream(vals + first + j)) : 0ull;
 
     int leader[KPT];
     if (fold) fold_duplicates<KIND, S::G, KPT>(k, valid, leader);
@@ -566,7 +584,7 @@ __device__ __forceinline__ void insert_tile(const View &v, const typename Traits
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
         res.st[j] = ST_EXISTS;
-        if (!(valid >> j & 1u) || leader[j] >= 0) continue;
+        if (!(valid >> j & 1u) || leader[j] >= 0 || (present >> j & 1u)) continue;
         const int side = side_index<KIND>(k[j]);
         if (side >= 0) {                         // key equal to a marker: side slot
             uint32_t won = 0;

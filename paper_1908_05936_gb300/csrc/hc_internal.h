@@ -22,7 +22,8 @@ struct LaunchShape {
 
 #define HC_DECLARE_KIND(NAME)                                                                                       \
     cudaError_t NAME##_range(int op, const View &v, int bb, const void *keys, const void *vals, long long n,        \
-                             uint8_t *out, void *vals_out, const LaunchShape &sh, cudaStream_t s);                  \
+                             uint8_t *out, void *vals_out, const LaunchShape &sh, const uint8_t *skip,              \
+                             cudaStream_t s);                                                                       \
     cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int sms,               \
                              cudaStream_t s);                                                                       \
     cudaError_t NAME##_dump(const View &v, unsigned long long phys, void *ko, void *vo, unsigned long long cap,     \

@@ -13,9 +13,9 @@ namespace hc {
 template <int KIND, int BB, int LB, int KPT>
 __global__ void __launch_bounds__(512)
 k_insert(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
-         uint8_t *status, int fold) {
+         uint8_t *status, int fold, const uint8_t *skip) {
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    insert_tile<KIND, BB, LB, KPT>(v, keys, vals, n, status, warp * Shape<BB, LB, KPT>::TILE, fold != 0);
+    insert_tile<KIND, BB, LB, KPT>(v, keys, vals, n, status, warp * Shape<BB, LB, KPT>::TILE, fold != 0, skip);
 }
 
 template <int KIND, int BB, int LB, int KPT>
@@ -34,26 +34,27 @@ k_erase(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *st
 }
 
 // ---------------------------------------------------------------- clear ---
-// Every slot EMPTY (all-ones bytes), then the slots past the capacity in the
-// last bucket become tombstones, and the header is zeroed.  32-byte stores.
+// Every key slot EMPTY (all-ones bytes, 32-byte stores), the header zeroed;
+// then the padding slots of the last bucket become tombstones.  Values need no
+// initialisation: a value is read only after its key was found.
 
 static __global__ void __launch_bounds__(256)
-k_fill_empty(unsigned char *slots, unsigned long long bytes, Header *hdr) {
+k_fill_empty(unsigned char *keys, unsigned long long bytes, Header *hdr) {
     const unsigned long long chunks = bytes / 32;
     const unsigned long long ones = ~0ull;
     for (unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
          c += (unsigned long long)gridDim.x * blockDim.x) {
-        asm volatile("st.global.v4.u64 [%0], {%1,%1,%1,%1};" ::"l"(slots + c * 32), "l"(ones) : "memory");
+        asm volatile("st.global.v4.u64 [%0], {%1,%1,%1,%1};" ::"l"(keys + c * 32), "l"(ones) : "memory");
     }
     if (blockIdx.x == 0 && threadIdx.x < sizeof(Header) / 8)
         reinterpret_cast<unsigned long long *>(hdr)[threadIdx.x] = 0ull;
 }
 
 template <int KIND>
-__global__ void k_pad_tombstones(unsigned char *slots, unsigned long long first, unsigned long long count) {
+__global__ void k_pad_tombstones(unsigned char *keys, unsigned long long first, unsigned long long count) {
     using T = Traits<KIND>;
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) *reinterpret_cast<typename T::Key *>(slots + (first + i) * T::SLOT) = T::TOMB;
+    if (i < count) reinterpret_cast<typename T::Key *>(keys)[first + i] = T::TOMB;
 }
 
 // ----------------------------------------------------------------- dump ---
@@ -62,26 +63,17 @@ __global__ void k_pad_tombstones(unsigned char *slots, unsigned long long first,
 
 template <int KIND>
 __global__ void __launch_bounds__(256)
-k_dump(View v, unsigned long long phys_slots, typename Traits<KIND>::Key *keys_out, typename Traits<KIND>::Val *vals_out,
+k_dump(View v, unsigned long long phys, typename Traits<KIND>::Key *keys_out, typename Traits<KIND>::Val *vals_out,
        unsigned long long cap) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    // iterate in whole-warp steps so every lane reaches the shuffles
+    // whole-warp steps so that every lane reaches the shuffles
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-         base < phys_slots; base += stride) {
+         base < phys; base += stride) {
         const unsigned long long i = base + lane;
-        Key key = T::EMPTY;
-        unsigned long long val = 0;
-        if (i < phys_slots) {
-            const unsigned char *slot = v.slots + i * T::SLOT;
-            key = *reinterpret_cast<const Key *>(slot);
-            if constexpr (T::MAP) {
-                if constexpr (sizeof(typename T::Val) == 4) val = *reinterpret_cast<const uint32_t *>(slot + 8);
-                else val = *reinterpret_cast<const unsigned long long *>(slot + 8);
-            }
-        }
+        const Key key = i < phys ? reinterpret_cast<const Key *>(v.keys)[i] : T::EMPTY;
         const bool live = key != T::EMPTY && key != T::TOMB;
         const unsigned m = __ballot_sync(0xffffffffu, live);
         if (!m) continue;
@@ -93,7 +85,7 @@ k_dump(View v, unsigned long long phys_slots, typename Traits<KIND>::Key *keys_o
             if (pos < cap) {
                 keys_out[pos] = key;
                 if constexpr (T::MAP) {
-                    if (vals_out) vals_out[pos] = (typename T::Val)val;
+                    if (vals_out) vals_out[pos] = reinterpret_cast<const typename T::Val *>(v.vals)[i];
                 }
             }
         }
@@ -113,38 +105,35 @@ k_dump(View v, unsigned long long phys_slots, typename Traits<KIND>::Key *keys_o
 }
 
 // --------------------------------------------------------------- rehash ---
-// Each stored key of the old slot array goes to the first EMPTY slot of its
-// probe sequence in the new array (keys are distinct, so no equality test).
+// Each stored key of the old arrays goes to the first EMPTY slot of its probe
+// sequence in the new arrays (keys are distinct, so no equality test; the new
+// table has no tombstones except its padding, which is never EMPTY).
 
 template <int KIND, int BB>
 __global__ void __launch_bounds__(256)
 k_rehash(View old_v, unsigned long long old_phys, View new_v) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
-    constexpr int SPB = BB / T::SLOT;
+    constexpr int SPB = BB / (int)sizeof(Key);
     uint32_t moved = 0;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
          base < old_phys; base += stride) {
         const unsigned long long i = base + (threadIdx.x & 31);
         if (i >= old_phys) continue;
-        const unsigned char *src = old_v.slots + i * T::SLOT;
-        const Key key = *reinterpret_cast<const Key *>(src);
+        const Key key = reinterpret_cast<const Key *>(old_v.keys)[i];
         if (key == T::EMPTY || key == T::TOMB) continue;
         unsigned long long val = 0;
-        if constexpr (T::MAP) {
-            if constexpr (sizeof(typename T::Val) == 4) val = *reinterpret_cast<const uint32_t *>(src + 8);
-            else val = *reinterpret_cast<const unsigned long long *>(src + 8);
-        }
+        if constexpr (T::MAP) val = reinterpret_cast<const typename T::Val *>(old_v.vals)[i];
         unsigned long long b = first_bucket(new_v, (unsigned long long)key);
         bool done = false;
         for (unsigned long long p = 0; p < new_v.nb && !done;) {
-            unsigned char *bucket = new_v.slots + b * BB;
+            Key *bucket = reinterpret_cast<Key *>(new_v.keys + b * BB);
             int s = 0;
             for (; s < SPB; ++s) {
                 Key ks;
-                if constexpr (sizeof(Key) == 4) ks = __ldcg(reinterpret_cast<const unsigned int *>(bucket + s * T::SLOT));
-                else ks = __ldcg(reinterpret_cast<const unsigned long long *>(bucket + s * T::SLOT));
+                if constexpr (sizeof(Key) == 4) ks = __ldcg(reinterpret_cast<const unsigned int *>(bucket + s));
+                else ks = __ldcg(reinterpret_cast<const unsigned long long *>(bucket + s));
                 if (ks == T::EMPTY) break;
             }
             if (s == SPB) {
@@ -152,8 +141,8 @@ k_rehash(View old_v, unsigned long long old_phys, View new_v) {
                 ++p;
                 continue;
             }
-            if (cas_key<KIND>(bucket + s * T::SLOT, T::EMPTY, key) == T::EMPTY) {
-                store_val<KIND>(bucket + s * T::SLOT, val);
+            if (cas_key<KIND>(reinterpret_cast<unsigned char *>(bucket + s), T::EMPTY, key) == T::EMPTY) {
+                store_val<KIND>(new_v, b * SPB + s, val);
                 done = true;
             }
             // a lost race re-reads the same bucket
@@ -175,7 +164,7 @@ inline unsigned grid_for(long long n, int tile, int block) {
 
 template <int KIND, int BB, int LB, int KPT>
 cudaError_t launch_range_shape(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
-                               void *vals_out, int block, int fold, cudaStream_t s) {
+                               void *vals_out, int block, int fold, const uint8_t *skip, cudaStream_t s) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Val = typename T::Val;
@@ -183,7 +172,7 @@ cudaError_t launch_range_shape(int op, const View &v, const void *keys, const vo
     const unsigned grid = grid_for(n, TILE, block);
     if (grid == 0) return cudaSuccess;
     if (op == OP_INSERT)
-        k_insert<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, (const Val *)vals, n, out, fold);
+        k_insert<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, (const Val *)vals, n, out, fold, skip);
     else if (op == OP_FIND)
         k_find<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, n, out, (Val *)vals_out);
     else
@@ -193,58 +182,58 @@ cudaError_t launch_range_shape(int op, const View &v, const void *keys, const vo
 
 template <int KIND, int BB, int LB>
 cudaError_t launch_range_kpt(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
-                             void *vals_out, const LaunchShape &sh, cudaStream_t s) {
+                             void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
     switch (sh.keys_per_group) {
-        case 1: return launch_range_shape<KIND, BB, LB, 1>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, s);
-        case 2: return launch_range_shape<KIND, BB, LB, 2>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, s);
-        case 4: return launch_range_shape<KIND, BB, LB, 4>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, s);
+        case 1: return launch_range_shape<KIND, BB, LB, 1>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, skip, s);
+        case 2: return launch_range_shape<KIND, BB, LB, 2>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, skip, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int KIND, int BB>
 cudaError_t launch_range_lb(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
-                            void *vals_out, const LaunchShape &sh, cudaStream_t s) {
-    switch (sh.lane_bytes) {
-        case 16: return launch_range_kpt<KIND, BB, 16>(op, v, keys, vals, n, out, vals_out, sh, s);
-        case 32: return launch_range_kpt<KIND, BB, 32>(op, v, keys, vals, n, out, vals_out, sh, s);
-        default: return cudaErrorInvalidValue;
-    }
+                            void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
+    if (sh.lane_bytes == 32) return launch_range_kpt<KIND, BB, 32>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+    if constexpr (BB >= 64)
+        if (sh.lane_bytes == 64) return launch_range_kpt<KIND, BB, 64>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+    if constexpr (BB >= 128)
+        if (sh.lane_bytes == 128) return launch_range_kpt<KIND, BB, 128>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+    return cudaErrorInvalidValue;
 }
 
 template <int KIND>
 cudaError_t launch_range(int op, const View &v, int bucket_bytes, const void *keys, const void *vals, long long n,
-                         uint8_t *out, void *vals_out, const LaunchShape &sh, cudaStream_t s) {
+                         uint8_t *out, void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
     switch (bucket_bytes) {
-        case 32: return launch_range_lb<KIND, 32>(op, v, keys, vals, n, out, vals_out, sh, s);
-        case 64: return launch_range_lb<KIND, 64>(op, v, keys, vals, n, out, vals_out, sh, s);
-        case 128: return launch_range_lb<KIND, 128>(op, v, keys, vals, n, out, vals_out, sh, s);
+        case 32: return launch_range_lb<KIND, 32>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+        case 64: return launch_range_lb<KIND, 64>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+        case 128: return launch_range_lb<KIND, 128>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int KIND>
-cudaError_t launch_clear(const View &v, unsigned long long phys_slots, unsigned long long capacity, int sm_count,
+cudaError_t launch_clear(const View &v, unsigned long long phys, unsigned long long capacity, int sm_count,
                          cudaStream_t s) {
-    const unsigned long long bytes = phys_slots * Traits<KIND>::SLOT;
+    const unsigned long long bytes = phys * sizeof(typename Traits<KIND>::Key);   // whole buckets: multiple of 32
     const unsigned long long chunks = bytes / 32;
     unsigned grid = (unsigned)std::min<unsigned long long>((chunks + 255) / 256, (unsigned long long)sm_count * 8);
     if (grid == 0) grid = 1;
-    k_fill_empty<<<grid, 256, 0, s>>>(v.slots, bytes, v.hdr);
-    if (phys_slots > capacity) {
-        const unsigned long long pad = phys_slots - capacity;
-        k_pad_tombstones<KIND><<<(unsigned)((pad + 127) / 128), 128, 0, s>>>(v.slots, capacity, pad);
+    k_fill_empty<<<grid, 256, 0, s>>>(v.keys, bytes, v.hdr);
+    if (phys > capacity) {
+        const unsigned long long pad = phys - capacity;
+        k_pad_tombstones<KIND><<<(unsigned)((pad + 127) / 128), 128, 0, s>>>(v.keys, capacity, pad);
     }
     return cudaGetLastError();
 }
 
 template <int KIND>
-cudaError_t launch_dump(const View &v, unsigned long long phys_slots, void *keys_out, void *vals_out,
-                        unsigned long long cap, int sm_count, cudaStream_t s) {
+cudaError_t launch_dump(const View &v, unsigned long long phys, void *keys_out, void *vals_out, unsigned long long cap,
+                        int sm_count, cudaStream_t s) {
     using T = Traits<KIND>;
-    unsigned grid = (unsigned)std::min<unsigned long long>((phys_slots + 255) / 256, (unsigned long long)sm_count * 8);
+    unsigned grid = (unsigned)std::min<unsigned long long>((phys + 255) / 256, (unsigned long long)sm_count * 8);
     if (grid == 0) grid = 1;
-    k_dump<KIND><<<grid, 256, 0, s>>>(v, phys_slots, (typename T::Key *)keys_out, (typename T::Val *)vals_out, cap);
+    k_dump<KIND><<<grid, 256, 0, s>>>(v, phys, (typename T::Key *)keys_out, (typename T::Val *)vals_out, cap);
     return cudaGetLastError();
 }
 
@@ -268,8 +257,9 @@ cudaError_t launch_rehash(const View &old_v, unsigned long long old_phys, const 
 #define HC_INSTANTIATE_KIND(KIND, NAME)                                                                             \
     namespace hc {                                                                                                  \
     cudaError_t NAME##_range(int op, const View &v, int bb, const void *keys, const void *vals, long long n,        \
-                             uint8_t *out, void *vals_out, const LaunchShape &sh, cudaStream_t s) {                 \
-        return launch_range<KIND>(op, v, bb, keys, vals, n, out, vals_out, sh, s);                                  \
+                             uint8_t *out, void *vals_out, const LaunchShape &sh, const uint8_t *skip,              \
+                             cudaStream_t s) {                                                                      \
+        return launch_range<KIND>(op, v, bb, keys, vals, n, out, vals_out, sh, skip, s);                            \
     }                                                                                                               \
     cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int sms,               \
                              cudaStream_t s) {                                                                      \

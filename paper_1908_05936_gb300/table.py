@@ -122,6 +122,24 @@ class Table:
                                    status.data_ptr() if status is not None else None, _stream_handle(stream)))
         return status
 
+    def insert_if_absent(self, keys: torch.Tensor, vals: torch.Tensor | None, found: torch.Tensor,
+                         status: torch.Tensor | bool = True, stream=None) -> torch.Tensor | None:
+        """Insert the keys whose ``found`` flag (from ``find`` on the same keys)
+        is 0; flagged keys get EXISTS without a probe."""
+        _check_tensor(keys, self.key_bytes, "keys")
+        _check_tensor(found, 1, "found")
+        n = keys.numel()
+        if self.is_map:
+            _check_tensor(vals, self.val_bytes, "vals")
+        if status is True:
+            status = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        elif status is False:
+            status = None
+        L.check(self.lib.hc_insert_if_absent(self.h, keys.data_ptr(), vals.data_ptr() if self.is_map else None,
+                                             found.data_ptr(), n, status.data_ptr() if status is not None else None,
+                                             _stream_handle(stream)))
+        return status
+
     def find(self, keys: torch.Tensor, found: torch.Tensor | None = None, vals_out: torch.Tensor | bool | None = True,
              stream=None):
         _check_tensor(keys, self.key_bytes, "keys")
