@@ -265,6 +265,27 @@ HC_API hc_rc hc_batch_launch(hc_batch *b, void *stream);
 /* Destroy a batch (synchronises the device first). */
 HC_API hc_rc hc_batch_destroy(hc_batch *b);
 
+/* The batched form for callers that must not allocate device memory: runs
+ * `n_items` items (at most 1024) exactly like a batch built by
+ * hc_batch_create and launched once, without a graph (cfg->use_graph must be
+ * 0), but allocates nothing.  Some callers cannot call cudaMalloc: a serving
+ * process whose device memory is all owned by another allocator's pool, or a
+ * latency-bound request loop where an allocation's implicit device-wide
+ * synchronisation would stall every other stream.  The descriptors and chunk
+ * counters live in one fixed array (about 105 KB) inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array; the counters are reset by each call, the
+ *     descriptors are overwritten.  Calls whose work overlaps on the GPU (on
+ *     different streams, or several host threads) race on the array and give
+ *     wrong results: order them on one stream.
+ *   - More than 1024 items is HC_ERR_ARG.
+ * The paper has no counterpart to this call. */
+HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg,
+                                  void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ EXPORTS = [
     "hc_abi_version", "hc_last_error", "hc_table_bytes", "hc_create", "hc_destroy", "hc_set_launch",
     "hc_get_launch", "hc_insert", "hc_insert_if_absent", "hc_find", "hc_erase", "hc_insert_host", "hc_find_host", "hc_erase_host",
     "hc_size", "hc_stats", "hc_status", "hc_clear", "hc_rehash", "hc_dump", "hc_batch_create",
-    "hc_batch_launch", "hc_batch_destroy",
+    "hc_batch_launch", "hc_batch_destroy", "hc_batch_run_noalloc",
 ]
 
 
@@ -95,6 +95,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_batch_create": (i32, [P(vp), P(BatchItem), i64, P(BatchConfig), vp]),
         "hc_batch_launch": (i32, [vp, vp]),
         "hc_batch_destroy": (i32, [vp]),
+        "hc_batch_run_noalloc": (i32, [P(BatchItem), i64, P(BatchConfig), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -11,6 +11,7 @@
 // granularity, and no launch is spent per table.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -303,6 +304,154 @@ HC_API hc_rc hc_batch_destroy(hc_batch *b) {
     cudaError_t e = cudaFree(b->d_mem);
     delete b;
     if (e != cudaSuccess) return bcuda(e, "cudaFree");
+    return HC_OK;
+}
+
+}  // extern "C"
+
+// ---- batched form without any device allocation --------------------------
+// hc_batch_create allocates its item descriptors and chunk counters with
+// cudaMalloc.  This variant keeps them in one file-scope device array instead,
+// for callers that must not allocate device memory themselves.  The array is
+// part of the library image: every GPU that loads the library holds it until
+// the process exits, and every call shares it.
+
+namespace {
+
+constexpr int kNoAllocMaxItems = 1024;   // items per call (104 KiB of descriptors)
+constexpr int kNoAllocMaxPhases = 12;    // 3 operations x 4 container kinds
+
+struct NoAllocScratch {
+    hc::BatchItemDev items[kNoAllocMaxItems];
+    unsigned long long counters[16];
+};
+
+}  // namespace
+
+// The scratch itself.  Host code must not take its address directly (on the
+// host this name is only a stand-in); the device address comes from
+// cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+namespace {
+
+std::mutex g_noalloc_mu;
+NoAllocScratch *g_noalloc_addr[64] = {nullptr};   // device address per device ordinal
+
+// Set-up, once per device, with that device current.
+hc_rc noalloc_scratch(int dev, NoAllocScratch **out) {
+    if (dev < 0 || dev >= 64) return bfail(HC_ERR_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return bcuda(e, "cudaGetSymbolAddress of the static batch scratch");
+        g_noalloc_addr[dev] = static_cast<NoAllocScratch *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return HC_OK;
+}
+
+// Host-side staging of the descriptors: per host thread, fixed size, so a
+// call allocates no memory on the host either.
+thread_local hc::BatchItemDev t_noalloc_items[kNoAllocMaxItems];
+
+}  // namespace
+
+extern "C" {
+
+HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg,
+                                  void *stream) {
+    if (n_items < 0 || (n_items > 0 && !items)) return bfail(HC_ERR_ARG, "bad item list");
+    if (n_items > kNoAllocMaxItems)
+        return bfail(HC_ERR_ARG, "hc_batch_run_noalloc takes at most 1024 items per call (got " +
+                                     std::to_string((long long)n_items) + ")");
+    hc_batch_config c{};
+    if (cfg) c = *cfg;
+    const int lb = c.lane_bytes;
+    const int kpt = c.keys_per_group ? c.keys_per_group : 1;
+    const int block = c.block ? c.block : 256;
+    const int tile = c.tile ? c.tile : 4096;
+    if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole bucket) or 32");
+    if (kpt != 1 && kpt != 2) return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
+    if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
+    if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
+    if (c.use_graph) return bfail(HC_ERR_ARG, "hc_batch_run_noalloc launches directly; use_graph must be 0");
+
+    // descriptors ordered by (op, kind), one phase per non-empty pair
+    hc::PhaseDesc phases[kNoAllocMaxPhases];
+    int n_phases = 0, n_dev = 0;
+    for (int op = 0; op < 3; ++op) {
+        for (int kind = 0; kind < 4; ++kind) {
+            hc::PhaseDesc ph{kind, op, n_dev, 0, 0, n_phases};
+            for (int64_t i = 0; i < n_items; ++i) {
+                const hc_batch_item &it = items[i];
+                if (!it.table || it.table->magic != HC_TABLE_MAGIC) return bfail(HC_ERR_ARG, "item with a bad table");
+                if (it.op < 0 || it.op > 2) return bfail(HC_ERR_ARG, "item with a bad op");
+                if (it.n < 0) return bfail(HC_ERR_ARG, "item with n < 0");
+                if (it.op != op || it.table->kind != kind || it.n == 0) continue;
+                const bool map = kind >= HC_MAP_I64_I32;
+                const int kb = kind == HC_SET_U32 ? 4 : 8;
+                if (!it.d_keys || reinterpret_cast<uintptr_t>(it.d_keys) % kb)
+                    return bfail(HC_ERR_ARG, "item keys NULL or misaligned");
+                if (op == HC_OP_INSERT && map && !it.d_vals) return bfail(HC_ERR_ARG, "insert item on a map without values");
+                if (op == HC_OP_FIND && !it.d_out) return bfail(HC_ERR_ARG, "find item without a found array");
+                hc::BatchItemDev &d = t_noalloc_items[n_dev++];
+                d = hc::BatchItemDev{};
+                d.v = it.table->view;
+                d.keys = it.d_keys;
+                d.vals = map ? it.d_vals : nullptr;
+                d.out = it.d_out;
+                d.vals_out = map ? it.d_vals_out : nullptr;
+                d.n = it.n;
+                d.chunk_begin = ph.n_chunks;
+                d.bb = it.table->bucket_bytes;
+                d.fold = op == HC_OP_FIND ? 0 : it.table->shape[op].fold;
+                ph.n_chunks += (it.n + tile - 1) / tile;
+                ph.n_items++;
+            }
+            if (ph.n_items) phases[n_phases++] = ph;
+        }
+    }
+    if (n_phases == 0) return HC_OK;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bcuda(e, "cudaGetDevice");
+    NoAllocScratch *scratch = nullptr;
+    hc_rc rc = noalloc_scratch(dev, &scratch);
+    if (rc != HC_OK) return rc;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return bcuda(e, "reading the SM count");
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // pageable source: the call returns once the descriptors are staged, so
+    // the per-thread array may be refilled by the next call
+    e = cudaMemcpyAsync(scratch->items, t_noalloc_items, (size_t)n_dev * sizeof(hc::BatchItemDev),
+                        cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bcuda(e, "copying the batch descriptors");
+    // the chunk counters keep the previous call's values: reset them first
+    hc::k_zero_counters<<<1, 32, 0, s>>>(scratch->counters, n_phases);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bcuda(e, "resetting the chunk counters");
+    for (int p = 0; p < n_phases; ++p) {
+        const hc::PhaseDesc &ph = phases[p];
+        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, lb, kpt);
+        int per_sm = c.blocks_per_sm;
+        if (per_sm <= 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0);
+            if (e != cudaSuccess) return bcuda(e, "querying occupancy");
+            if (per_sm <= 0) per_sm = 1;
+        }
+        long long g = (long long)sms * per_sm;
+        const long long need = (ph.n_chunks * 32 + block - 1) / block;
+        if (g > need) g = need;
+        k<<<(unsigned)(g > 0 ? g : 1), block, 0, s>>>(scratch->items + ph.item0, ph.n_items, ph.n_chunks, tile,
+                                                     scratch->counters + ph.counter);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(e, "launching a batch phase");
+    }
     return HC_OK;
 }
 
