@@ -45,6 +45,24 @@ __global__ void k_value_of(unsigned long long *out, const unsigned long long *ke
         out[i] = fin(keys[i] + kGolden);
 }
 
+// Zipf keys: r = number of CDF entries <= u (u from the stream, top 53 bits),
+// key = finaliser(r ^ salt): the inverse-CDF rule of
+// workloads.recipes.zipf_keys.
+__global__ void k_zipf(unsigned long long *out, long long n, unsigned long long base, const double *cdf,
+                       long long n_ranks, unsigned long long salt) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long z = fin(base + (unsigned long long)(i + 1) * kGolden);
+        const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        long long lo = 0, hi = n_ranks;            // searchsorted(cdf, u, side="right")
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (cdf[mid] <= u) lo = mid + 1;
+            else hi = mid;
+        }
+        out[i] = fin((unsigned long long)lo ^ salt);
+    }
+}
+
 unsigned grid_for(long long n) {
     long long g = (n + 255) / 256;
     return (unsigned)(g < 1 ? 1 : (g > 65536 ? 65536 : g));
@@ -62,6 +80,14 @@ GEN_API int hcgen_affine(void *out, long long n, unsigned long long n_pop, unsig
                          unsigned long long base, void *stream) {
     if (n <= 0) return 0;
     k_affine<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((unsigned long long *)out, n, n_pop, a, c, base);
+    return (int)cudaGetLastError();
+}
+
+GEN_API int hcgen_zipf(void *out, long long n, unsigned long long base, const void *cdf, long long n_ranks,
+                       unsigned long long salt, void *stream) {
+    if (n <= 0) return 0;
+    k_zipf<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((unsigned long long *)out, n, base, (const double *)cdf,
+                                                         n_ranks, salt);
     return (int)cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@ def load():
         lib.hcgen_stream.argtypes = [vp, ll, ll, ull, ctypes.c_int, vp]
         lib.hcgen_affine.argtypes = [vp, ll, ull, ull, ull, ull, vp]
         lib.hcgen_value_of.argtypes = [vp, vp, ll, vp]
+        lib.hcgen_zipf.argtypes = [vp, ll, ull, vp, ll, ull, vp]
         _lib = lib
     return _lib
 
@@ -86,4 +87,15 @@ def value_of(keys):
     import torch
     out = torch.empty_like(keys)
     _check(load().hcgen_value_of(out.data_ptr(), keys.data_ptr(), keys.numel(), _stream()))
+    return out
+
+
+def zipf_keys(table: int, stream: int, n: int, cdf_dev, seed: int = 0):
+    """GPU twin of ``recipes.zipf_keys``; ``cdf_dev`` is the float64 CDF as a
+    CUDA tensor."""
+    import torch
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    salt = (table & 0xFFFF) << 48
+    _check(load().hcgen_zipf(out.data_ptr(), n, sm.stream_base(stream, seed), cdf_dev.data_ptr(), cdf_dev.numel(),
+                             salt, _stream()))
     return out

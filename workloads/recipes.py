@@ -117,3 +117,49 @@ def multi_table_ops(slots: int, t: int, seed: int = 0, ops_fraction: float = 0.5
         q = q[sm.permutation(len(q), 31, seed + t)]
     er = ins[sm.affine_sample(n_ins, min(n_er, n_ins), 32, seed + t)] if n_ins else ins[:0]
     return TableOps(int(slots), ins, q, er)
+
+
+# ---------------------------------------------------------------------------
+# Served workload: Poisson arrivals of insert/find/erase requests on resident
+# map<u64,u64> tables, sizes log-uniform in [1, 2^20], Zipf(1.1) keys
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class Request:
+    rid: int
+    table: int
+    op: int            # 0 insert, 1 find, 2 erase
+    n: int
+    arrival: float     # seconds from the start
+    key_stream: int    # keys = zipf_keys(table, key_stream, n)
+
+
+def zipf_cdf(n_ranks: int, s: float = 1.1) -> np.ndarray:
+    """CDF of a Zipf(s) law over ranks 1..n_ranks (float64)."""
+    w = np.arange(1, n_ranks + 1, dtype=np.float64) ** (-s)
+    c = np.cumsum(w)
+    return c / c[-1]
+
+
+def zipf_keys(table: int, stream: int, n: int, cdf: np.ndarray, seed: int = 0) -> np.ndarray:
+    """n keys of one table: Zipf ranks by inverse CDF, mapped to uint64 keys
+    through splitmix64(rank ^ table << 48) so hot keys are scattered."""
+    u = sm.uniform01(stream, seed, 0, n)
+    rank = np.searchsorted(cdf, u, side="right").astype(np.uint64)
+    return sm.mix(rank ^ (np.uint64(table) << np.uint64(48)))
+
+
+def served_requests(n_requests: int, n_tables: int, rate_per_s: float, seed: int = 0,
+                    mix=(0.4, 0.5, 0.1), max_log2: int = 20) -> list[Request]:
+    """Poisson arrivals (exponential gaps at `rate_per_s`), uniform table,
+    op drawn from `mix`, size floor(2^U(0, max_log2))."""
+    u = sm.uniform01(3000, seed, 0, 4 * n_requests).reshape(4, n_requests)
+    gaps = -np.log(np.maximum(u[0], 1e-300)) / rate_per_s
+    arrival = np.cumsum(gaps) - gaps[0]
+    table = np.minimum((u[1] * n_tables).astype(np.int64), n_tables - 1)
+    cm = np.cumsum(mix)
+    op = np.searchsorted(cm / cm[-1], u[2], side="right")
+    size = np.maximum(1, np.floor(np.exp2(u[3] * max_log2)).astype(np.int64))
+    return [Request(i, int(table[i]), int(op[i]), int(size[i]), float(arrival[i]), 4000 + i)
+            for i in range(n_requests)]

@@ -33,13 +33,13 @@ class RGBDParams:
     block_voxels: int = 8         # block edge in voxels (64 mm)
     width: float = 30.0           # corridor width (m)
     wall_height: float = 5.0      # m
-    speed: float = 1.45           # camera advance per frame (m)
+    speed: float = 0.8            # camera advance per frame (m)
     near: float = 0.5             # m
-    depth: float = 15.0           # visible band along y (m)
+    depth: float = 12.0           # visible band along y (m)
     cam_height: float = 1.6       # m
     sway: float = 3.0             # lateral camera sway amplitude (m)
-    sigma0: float = 0.02          # depth noise at zero range (m)
-    sigma1: float = 0.0012        # depth noise growth (1/m)
+    sigma0: float = 0.01          # depth noise at zero range (m)
+    sigma1: float = 0.0003        # depth noise growth (1/m)
     sphere_every: float = 5.0     # one sphere per this many metres of corridor
     seed: int = 0
 
