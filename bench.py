@@ -51,6 +51,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=22)
+    ap.add_argument("--workload", default="map_sweep", choices=["map_sweep", "multi_table", "served", "rgbd"])
+    ap.add_argument("--rgbd-slots", type=int, default=12_500_000)
+    ap.add_argument("--rgbd-hash", type=int, default=1, help="1 = the paper's spatial hash, 0 = mix64")
+    ap.add_argument("--tables", type=int, default=1024)
+    ap.add_argument("--tile", type=int, default=4096)
+    ap.add_argument("--requests", type=int, default=3000)
+    ap.add_argument("--served-tables", type=int, default=64)
+    ap.add_argument("--served-slots", type=int, default=56_000_000)
     return ap.parse_args()
 
 
@@ -151,7 +159,7 @@ def run_gpu(args, rank: int, world: int):
     found = torch.empty(B, dtype=torch.uint8, device=dev)
     vout = torch.empty(B, dtype=torch.int64, device=dev)
 
-    bb = args.bucket_bytes or 32
+    bb = args.bucket_bytes or 64
     t = Table(L.MAP_U64_U64, wl.slots, bucket_bytes=bb)
     for op in (0, 1, 2):
         t.set_launch(op, lane_bytes=args.lane_bytes, keys_per_group=args.kpt, block=args.block)
@@ -247,6 +255,7 @@ def run_gpu(args, rank: int, world: int):
     dom_ms = summary[dom]["ms_total"] / len(per[dom])
     achieved = BYTES_PER_OP[kinds[dom]] * dom_n / (dom_ms * 1e-3) / 1e9
     peak, peak_src = hbm_peak()
+    ceiling = random_read_ceiling(torch, L)
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mops/s", "n_gpus": world, "steps": args.steps,
@@ -260,6 +269,7 @@ def run_gpu(args, rank: int, world: int):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": None, "bytes_per_op": BYTES_PER_OP[kinds[dom]]},
+        "random_read_ceiling": ceiling,
         "clocks": clk,
         "gpu_launches": len(calls) * world,
         "check": {"size_after_step": size_after, "expected": expected_size},
@@ -302,6 +312,22 @@ def run_e2e(t, wl, fill, vals, hit, miss, er, stream):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 2)}
 
 
+def random_read_ceiling(torch, L):
+    """Measured rate of random 32-byte reads over a 2 GiB buffer (larger than
+    L2): the ceiling of a probe-bound operation on this device."""
+    import ctypes
+    buf = torch.empty(1 << 31, dtype=torch.uint8, device="cuda")
+    ms = ctypes.c_float()
+    n = 1 << 26
+    L.check(L.load().hc_measure_random_reads(buf.data_ptr(), buf.numel(), n, 5, ctypes.byref(ms),
+                                             torch.cuda.current_stream().cuda_stream))
+    del buf
+    rate = n / (ms.value * 1e-3)
+    return {"reads_per_s": round(rate / 1e9, 2), "unit": "G random 32-byte reads/s",
+            "line_traffic_gbs": round(rate * 128 / 1e9, 1),
+            "note": "each random read moves one 128-byte line from HBM on this GPU"}
+
+
 def hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -339,8 +365,262 @@ def run_oracle_sample(args, sample_log2: int):
             "seconds": round(dt, 2), "host_cores_available": os.cpu_count()}
 
 
+# ------------------------------------------------ multi-table workload --
+
+def run_multi_table(args):
+    """1024 set<u64> tables, capacities log-uniform in 2^10..2^22; each gets
+    0.5 x capacity ops (60 % insert, 30 % find, 10 % erase).  The plain form
+    is 3 x 1024 range calls; the batched form is one CUDA graph of three
+    persistent phase kernels.  A step is the op batch of every table; the
+    tables are cleared between steps, outside the timed intervals."""
+    import torch
+    from paper_1908_05936_gb300 import _lib as L
+    from paper_1908_05936_gb300 import build
+    from paper_1908_05936_gb300.batch import Batch, Item
+    from paper_1908_05936_gb300.table import Table, to_device
+    from workloads import recipes
+
+    build.build()
+    n_tables = args.tables
+    slots = recipes.multi_table_slots(n_tables)
+    ops = [recipes.multi_table_ops(int(s), t) for t, s in enumerate(slots)]
+    n_ops = sum(len(o.insert_keys) + len(o.find_keys) + len(o.erase_keys) for o in ops)
+    bb = args.bucket_bytes or 128
+    arms = {}
+    for arm in ("plain", "batched"):
+        tabs = [Table(L.SET_U64, int(s), bucket_bytes=bb) for s in slots]
+        items = []
+        for t, o in zip(tabs, ops):
+            ki, kf, ke = to_device(o.insert_keys), to_device(o.find_keys), to_device(o.erase_keys)
+            items += [Item(t, L.OP_INSERT, ki, None, torch.empty(ki.numel(), dtype=torch.uint8, device="cuda")),
+                      Item(t, L.OP_FIND, kf, None, torch.empty(kf.numel(), dtype=torch.uint8, device="cuda")),
+                      Item(t, L.OP_ERASE, ke, None, torch.empty(ke.numel(), dtype=torch.uint8, device="cuda"))]
+        batch = Batch(items, tile=args.tile, use_graph=True) if arm == "batched" else None
+        stream = torch.cuda.current_stream()
+
+        def step():
+            if batch is not None:
+                batch.launch()
+                return 3
+            for it in items:
+                if it.op == L.OP_INSERT:
+                    it.table.insert(it.keys, None, status=it.out)
+                elif it.op == L.OP_FIND:
+                    it.table.find(it.keys, found=it.out, vals_out=False)
+                else:
+                    it.table.erase(it.keys, status=it.out)
+            return len(items)
+
+        times, launches = [], 0
+        for i in range(args.warmup + args.steps):
+            for t in tabs:
+                t.clear()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nl = step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(a.elapsed_time(b))
+                launches += nl
+        sizes = sum(t.size() for t in tabs)
+        arms[arm] = {"ms_per_step": round(statistics.median(times), 3), "mops": round(n_ops / statistics.median(times) / 1e3, 1),
+                     "launches_per_step": launches // args.steps, "live_after": sizes}
+        for t in tabs:
+            t.close()
+        if batch is not None:
+            batch.close()
+        del items
+        torch.cuda.empty_cache()
+    assert arms["plain"]["live_after"] == arms["batched"]["live_after"], "plain and batched forms disagree"
+    return {"metric": "multi-table batched vs plain: ms per step and Mops/s", "value": arms["batched"]["mops"],
+            "unit": "Mops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": arms["batched"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded splitmix64 keys)",
+            "config": {"workload": f"{n_tables} set<u64> tables, capacities round(2^U(10,22)), 0.5 x capacity ops "
+                                   "60/30/10 insert/find/erase", "total_slots": int(slots.sum()), "ops_per_step": n_ops,
+                       "bucket_bytes": bb, "tile": args.tile},
+            "plain": arms["plain"], "batched": arms["batched"],
+            "speedup": round(arms["plain"]["ms_per_step"] / arms["batched"]["ms_per_step"], 3),
+            "gpu_launches": arms["batched"]["launches_per_step"] * args.steps}
+
+
+# ------------------------------------------------------ RGB-D workload --
+
+def rgbd_frames(params, workers: int = 8):
+    """All frames' candidate keys and values (host), generated by a process
+    pool started with spawn (safe next to an initialised CUDA context)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from workloads import rgbd
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        keys = list(ex.map(_rgbd_frame, [(params, f) for f in range(params.frames)], chunksize=4))
+    return keys, [rgbd.values_of(k) for k in keys]
+
+
+def _rgbd_frame(arg):
+    from workloads import rgbd
+    params, f = arg
+    return rgbd.frame_keys(params, f)
+
+
+def run_rgbd(args):
+    """map<int64 packed block, int32>: 300 frames x 400k candidate blocks of
+    the synthetic RGB-D stream; per frame, find the candidates and insert the
+    missing ones.  Eager (two launches per frame) against one CUDA graph
+    holding the whole stream."""
+    import torch
+    from paper_1908_05936_gb300 import _lib as L
+    from paper_1908_05936_gb300 import build
+    from paper_1908_05936_gb300.table import Table, to_device
+    from workloads import rgbd
+
+    build.build()
+    params = rgbd.RGBDParams()
+    t0 = time.perf_counter()
+    keys, vals = rgbd_frames(params, workers=min(16, os.cpu_count() or 4))
+    gen_s = time.perf_counter() - t0
+    capacity = args.rgbd_slots
+    tab = Table(L.MAP_I64_I32, capacity, bucket_bytes=args.bucket_bytes or 64, hash_mode=args.rgbd_hash)
+    d_keys = [to_device(k) for k in keys]
+    d_vals = [to_device(v) for v in vals]
+    found = [torch.empty(len(k), dtype=torch.uint8, device="cuda") for k in keys]
+    status = [torch.empty(len(k), dtype=torch.uint8, device="cuda") for k in keys]
+
+    def stream_all():
+        for f in range(params.frames):
+            tab.find(d_keys[f], found=found[f], vals_out=False)
+            tab.insert_if_absent(d_keys[f], d_vals[f], found[f], status=status[f])
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        stream_all()
+    res = {}
+    for arm in ("eager", "graph"):
+        times = []
+        for i in range(args.warmup + args.steps):
+            tab.clear()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            if arm == "graph":
+                g.replay()
+            else:
+                stream_all()
+            b.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(a.elapsed_time(b))
+        ms = statistics.median(times)
+        res[arm] = {"ms_per_stream": round(ms, 3), "ms_per_frame": round(ms / params.frames, 4),
+                    "mcandidates_per_s": round(params.frames * params.per_frame / ms / 1e3, 1)}
+    final = tab.size()
+    pres = [float(found[f].float().mean()) for f in range(params.frames)]
+    tab.close()
+    return {"metric": "RGB-D stream: per-frame find-then-insert time and candidates/s",
+            "value": res["graph"]["mcandidates_per_s"], "unit": "M candidates/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["graph"]["ms_per_stream"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i64/i32",
+            "data": "synthetic RGB-D voxel-block stream (sphere + planes, seeded)",
+            "config": {"workload": f"map<i64,i32> {capacity} slots, {params.frames} frames x {params.per_frame} "
+                                   "candidate blocks, find then insert missing", "hash_mode": args.rgbd_hash,
+                       "generation_s": round(gen_s, 1)},
+            "eager": res["eager"], "graph": res["graph"], "final_blocks": final,
+            "final_load_factor": round(final / capacity, 4), "present_mean": round(float(np.mean(pres[1:])), 4),
+            "gpu_launches": 2 * params.frames}
+
+
+# ---------------------------------------------------- served workload --
+
+def run_served(args):
+    """64 resident map<u64,u64> tables (56M slots each, ~57 GB), prefilled to
+    load factor 0.5; Poisson arrivals of insert/find/erase requests (40/50/10)
+    with sizes floor(2^U(0,20)) and Zipf(1.1) keys over 2^24 ranks per table.
+    First the plain one-launch-per-request path serves every request as fast
+    as it can (its capacity); then both forms serve real-time arrivals at
+    50 %, 80 % and 100 % of that capacity."""
+    import torch
+    from paper_1908_05936_gb300 import _lib as L
+    from paper_1908_05936_gb300 import build
+    from paper_1908_05936_gb300.serve import Server, ServedRequest
+    from paper_1908_05936_gb300.table import Table
+    from workloads import gpu as G
+    from workloads import recipes
+
+    build.build()
+    n_tables, slots = args.served_tables, args.served_slots
+    tabs = [Table(L.MAP_U64_U64, slots, bucket_bytes=args.bucket_bytes or 64) for _ in range(n_tables)]
+    prefill = slots // 2
+    for t, tab in enumerate(tabs):
+        for off in range(0, prefill, 1 << 26):
+            k = G.stream_u64(7000 + t, 0, off, min(1 << 26, prefill - off))
+            tab.insert(k, G.value_of(k), status=False)
+    torch.cuda.synchronize()
+    base = recipes.served_requests(args.requests, n_tables, 1.0)
+    cdf = torch.from_numpy(recipes.zipf_cdf(1 << 24)).cuda()
+    total = sum(q.n for q in base)
+    keys_h = torch.empty(total, dtype=torch.int64, pin_memory=True)
+    vals_h = torch.empty(total, dtype=torch.int64, pin_memory=True)
+    off = 0
+    spans = []
+    for q in base:
+        k = G.zipf_keys(q.table, q.key_stream, q.n, cdf)
+        keys_h[off:off + q.n].copy_(k)
+        if q.op == L.OP_INSERT:
+            vals_h[off:off + q.n].copy_(G.value_of(k))
+        spans.append((off, q.n))
+        off += q.n
+    torch.cuda.synchronize()
+
+    def requests(rate):
+        return [ServedRequest(q.rid, q.table, q.op, keys_h[o:o + n], vals_h[o:o + n] if q.op == L.OP_INSERT else None,
+                              q.arrival / rate) for q, (o, n) in zip(base, spans)]
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    plain = Server(tabs, lanes=4, depth=2, merge=False)
+    merged = Server(tabs, lanes=4, depth=2, merge=True)
+    cap = plain.run(requests(1.0), realtime=False)
+    cap_rate = cap["requests"] / cap["wall_s"]
+    cap_merged = merged.run(requests(1.0), realtime=False)
+    loads = {}
+    for frac in (0.5, 0.8, 1.0):
+        rate = frac * cap_rate
+        loads[f"{int(frac * 100)}%"] = {"rate_req_per_s": round(rate, 1),
+                                        "plain": plain.run(requests(rate), realtime=True),
+                                        "merged": merged.run(requests(rate), realtime=True)}
+    clk = clocks.stop()
+    budget = merged.hbm_budget()
+    for t in tabs:
+        t.close()
+    head = loads["80%"]
+    return {"metric": "served p50/p99 latency and Mops/s vs the plain one-launch-per-request path",
+            "value": head["merged"]["mops"], "unit": "Mops/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded Poisson arrivals, Zipf(1.1) keys)",
+            "config": {"workload": f"{n_tables} map<u64,u64> x {slots} slots, prefilled to LF 0.5, {args.requests} "
+                                   "requests, sizes floor(2^U(0,20)), 40/50/10 insert/find/erase, Zipf(1.1) over 2^24",
+                       "ops": total, "hbm": budget},
+            "capacity": {"plain": cap, "merged": cap_merged, "plain_req_per_s": round(cap_rate, 1)},
+            "loads": loads, "clocks": clk}
+
+
 def main():
     args = parse()
+    if args.workload == "multi_table":
+        print(json.dumps(run_multi_table(args)))
+        return
+    if args.workload == "served":
+        print(json.dumps(run_served(args)))
+        return
+    if args.workload == "rgbd":
+        print(json.dumps(run_rgbd(args)))
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -225,6 +225,15 @@ HC_API hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream);
 HC_API hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap,
               int64_t *n_out, void *stream);
 
+/* Device calibration: the time of one launch of n_reads reads of 32 bytes at
+ * pseudo-random 32-byte-aligned offsets of d_buf (buf_bytes >= 64, 32-byte
+ * aligned; its last 32 bytes may be overwritten), averaged over `reps`
+ * launches after one warm-up, in *ms_per_launch.  Every probe of a table is a
+ * random read, so n_reads / time is the ceiling of a probe-bound operation on
+ * this device.  Synchronises `stream`.  The paper has no counterpart. */
+HC_API hc_rc hc_measure_random_reads(const void *d_buf, int64_t buf_bytes, int64_t n_reads, int32_t reps,
+                                     float *ms_per_launch, void *stream);
+
 /* ---- batched form: many tables in one persistent launch -----------------
  * Not in the paper (it has one container per call); it schedules many of the
  * Section 4.1 range calls at once.  A batch holds items; each item is one
@@ -264,6 +273,21 @@ HC_API hc_rc hc_batch_launch(hc_batch *b, void *stream);
 
 /* Destroy a batch (synchronises the device first). */
 HC_API hc_rc hc_batch_destroy(hc_batch *b);
+
+/* Device scratch bytes hc_batch_run needs for n_items items (-1 if n_items
+ * is outside [0, 4096]). */
+HC_API int64_t hc_batch_scratch_bytes(int64_t n_items);
+
+/* Run n_items items once as a batch (the same phases and scheduling as a
+ * batch from hc_batch_create, without a graph), with the descriptors and
+ * chunk counters in the caller's device buffer d_scratch (256-byte aligned,
+ * at least hc_batch_scratch_bytes(n_items) bytes).  Nothing is allocated and
+ * nothing is kept, so a caller forming a new batch for every dispatch (a
+ * request loop) pays no allocation.  Calls on different streams need
+ * different scratch buffers; calls ordered on one stream may share one.  At
+ * most 4096 items. */
+HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg, void *d_scratch,
+                          int64_t scratch_bytes, void *stream);
 
 /* The batched form for callers that must not allocate device memory: runs
  * `n_items` items (at most 1024) exactly like a batch built by

@@ -38,11 +38,21 @@ hc_rc cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 bool valid_kind(int kind) { return kind >= HC_SET_U32 && kind <= HC_MAP_U64_U64; }
+bool is_map(int kind) { return kind == HC_MAP_I64_I32 || kind == HC_MAP_U64_U64; }
 int key_bytes(int kind) { return kind == HC_SET_U32 ? 4 : 8; }
 int val_bytes(int kind) { return kind == HC_MAP_I64_I32 ? 4 : (kind == HC_MAP_U64_U64 ? 8 : 0); }
-// bytes a slot holds across the key and value arrays
+// bytes a slot holds: key plus value
 int slot_bytes(int kind) { return valid_kind(kind) ? key_bytes(kind) + val_bytes(kind) : 0; }
-bool is_map(int kind) { return kind == HC_MAP_I64_I32 || kind == HC_MAP_U64_U64; }
+// slots per bucket of bb bytes: keys only for sets; for maps the largest
+// power of two of (key, value) slots that fits (same rule as the kernels)
+int slots_per_bucket(int kind, int bb) {
+    if (!is_map(kind)) return bb / key_bytes(kind);
+    int n = bb / slot_bytes(kind), p = 1;
+    while (p * 2 <= n && p < 16) p *= 2;
+    return p;
+}
+// bytes of a bucket's key region (what a probe reads)
+int key_region_bytes(int kind, int bb) { return slots_per_bucket(kind, bb) * key_bytes(kind); }
 
 int sm_count_of(int dev) {
     static std::mutex mu;
@@ -74,29 +84,26 @@ hc_rc check_config(int kind, const hc_config *cfg, int *bb, int *hash_mode, unsi
     return HC_OK;
 }
 
-// Device memory of a table: [header 256 B][keys: phys slots][values: phys
-// slots (maps)], each part starting on a 256-byte boundary.
+// Device memory of a table: [header 256 B][nb buckets of bb bytes].
 struct Geometry {
-    long long nb, phys, vals_off, bytes;
+    long long nb, phys, bytes;
     int pad_from;
 };
 
 Geometry geometry(int kind, long long slots, int bb) {
-    const long long spb = bb / key_bytes(kind);
+    const long long spb = slots_per_bucket(kind, bb);
     Geometry g;
     g.nb = (slots + spb - 1) / spb;
     g.phys = g.nb * spb;
     g.pad_from = (int)(spb - (g.phys - slots));
-    g.vals_off = (long long)sizeof(hc::Header) + (g.phys * key_bytes(kind) + 255) / 256 * 256;
-    g.bytes = g.vals_off + (g.phys * val_bytes(kind) + 255) / 256 * 256;
+    g.bytes = (long long)sizeof(hc::Header) + (g.nb * bb + 255) / 256 * 256;
     return g;
 }
 
-hc::View make_view(void *mem, const Geometry &g, unsigned long long seed, int hash_mode, int kind) {
+hc::View make_view(void *mem, const Geometry &g, unsigned long long seed, int hash_mode) {
     hc::View v;
     v.hdr = static_cast<hc::Header *>(mem);
-    v.keys = static_cast<unsigned char *>(mem) + sizeof(hc::Header);
-    v.vals = val_bytes(kind) ? static_cast<unsigned char *>(mem) + g.vals_off : nullptr;
+    v.buckets = static_cast<unsigned char *>(mem) + sizeof(hc::Header);
     v.nb = g.nb;
     v.seed = seed;
     v.hash_mode = hash_mode;
@@ -118,10 +125,10 @@ cudaError_t dispatch_range(int kind, int op, const hc::View &v, int bb, const vo
 cudaError_t dispatch_clear(const hc_table *t, const hc::View &v, long long phys, long long cap, cudaStream_t s) {
     const int sms = sm_count_of(t->device);
     switch (t->kind) {
-        case HC_SET_U32: return hc::set_u32_clear(v, phys, cap, sms, s);
-        case HC_SET_U64: return hc::set_u64_clear(v, phys, cap, sms, s);
-        case HC_MAP_I64_I32: return hc::map_i64_i32_clear(v, phys, cap, sms, s);
-        default: return hc::map_u64_u64_clear(v, phys, cap, sms, s);
+        case HC_SET_U32: return hc::set_u32_clear(v, phys, cap, t->bucket_bytes, sms, s);
+        case HC_SET_U64: return hc::set_u64_clear(v, phys, cap, t->bucket_bytes, sms, s);
+        case HC_MAP_I64_I32: return hc::map_i64_i32_clear(v, phys, cap, t->bucket_bytes, sms, s);
+        default: return hc::map_u64_u64_clear(v, phys, cap, t->bucket_bytes, sms, s);
     }
 }
 
@@ -176,7 +183,8 @@ hc_rc run_range(hc_table *t, int op, const void *keys, const void *vals, long lo
                 cudaStream_t s, const uint8_t *skip = nullptr) {
     hc_rc rc = range_checks(t, op, keys, vals, n, out, vals_out);
     if (rc != HC_OK || n == 0) return rc;
-    const hc::LaunchShape &sh = t->shape[op];
+    hc::LaunchShape sh = t->shape[op];
+    sh.sms = sm_count_of(t->device);
     cudaError_t e = dispatch_range(t->kind, op, t->view, t->bucket_bytes, keys, is_map(t->kind) ? vals : nullptr, n,
                                    out, is_map(t->kind) ? vals_out : nullptr, sh, skip, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the range kernel");
@@ -290,10 +298,10 @@ hc_rc hc_create(hc_table **out, int32_t kind, int64_t slots, const hc_config *cf
         delete t;
         return fail(HC_ERR_OOM, "cudaMalloc of %lld bytes failed: %s", (long long)g.bytes, cudaGetErrorString(e));
     }
-    t->view = make_view(t->d_mem, g, seed, hm, kind);
-    // one thread per key reading the whole bucket, one key in flight,
+    t->view = make_view(t->d_mem, g, seed, hm);
+    // one thread per key reading the bucket's keys, one key in flight,
     // 128-thread blocks: the best shape of the sweeps on GB300 for uniform keys
-    for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{bb, 1, 128, 0};
+    for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{key_region_bytes(kind, bb), 1, 128, 0, 0};
     e = dispatch_clear(t, t->view, t->phys, t->capacity, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         cudaFree(t->d_mem);
@@ -332,8 +340,14 @@ hc_rc hc_set_launch(hc_table *t, int32_t op, const hc_launch *shape) {
     if (shape->keys_per_group) sh.keys_per_group = shape->keys_per_group;
     if (shape->block) sh.block = shape->block;
     if (shape->fold_duplicates) sh.fold = shape->fold_duplicates == 1 ? 1 : 0;
-    if ((sh.lane_bytes != 32 && sh.lane_bytes != 64 && sh.lane_bytes != 128) || sh.lane_bytes > t->bucket_bytes)
-        return fail(HC_ERR_ARG, "lane_bytes must be 32, 64 or 128 and at most the bucket size");
+    const int krb = key_region_bytes(t->kind, t->bucket_bytes);
+    const bool full = is_map(t->kind) && sh.lane_bytes == t->bucket_bytes;   // keys and values in one read
+    const bool lb_ok = (sh.lane_bytes == 16 && is_map(t->kind)) || sh.lane_bytes == 32 || sh.lane_bytes == 64 ||
+                       sh.lane_bytes == 128;
+    if (!full && (!lb_ok || sh.lane_bytes > krb))
+        return fail(HC_ERR_ARG,
+                    "lane_bytes must be 32, 64 or 128 (16 for maps) and at most the %d-byte key region, or the whole "
+                    "bucket for maps", krb);
     if (sh.keys_per_group != 1 && sh.keys_per_group != 2)
         return fail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
     if (sh.block < 64 || sh.block > 512 || sh.block % 32)
@@ -448,7 +462,7 @@ hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
         (void)cudaGetLastError();
         return fail(HC_ERR_OOM, "cudaMalloc of %lld bytes failed: %s", (long long)g.bytes, cudaGetErrorString(e));
     }
-    hc::View nv = make_view(mem, g, t->view.seed, t->view.hash_mode, t->kind);
+    hc::View nv = make_view(mem, g, t->view.seed, t->view.hash_mode);
     e = dispatch_clear(t, nv, g.phys, new_slots, s);
     const int sms = sm_count_of(t->device);
     if (e == cudaSuccess) {
@@ -493,10 +507,12 @@ hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap, int6
     void *vo = is_map(t->kind) ? d_vals_out : nullptr;
     cudaError_t e;
     switch (t->kind) {
-        case HC_SET_U32: e = hc::set_u32_dump(t->view, t->phys, d_keys_out, vo, cap, sms, s); break;
-        case HC_SET_U64: e = hc::set_u64_dump(t->view, t->phys, d_keys_out, vo, cap, sms, s); break;
-        case HC_MAP_I64_I32: e = hc::map_i64_i32_dump(t->view, t->phys, d_keys_out, vo, cap, sms, s); break;
-        default: e = hc::map_u64_u64_dump(t->view, t->phys, d_keys_out, vo, cap, sms, s); break;
+        case HC_SET_U32: e = hc::set_u32_dump(t->view, t->phys, d_keys_out, vo, cap, t->bucket_bytes, sms, s); break;
+        case HC_SET_U64: e = hc::set_u64_dump(t->view, t->phys, d_keys_out, vo, cap, t->bucket_bytes, sms, s); break;
+        case HC_MAP_I64_I32:
+            e = hc::map_i64_i32_dump(t->view, t->phys, d_keys_out, vo, cap, t->bucket_bytes, sms, s);
+            break;
+        default: e = hc::map_u64_u64_dump(t->view, t->phys, d_keys_out, vo, cap, t->bucket_bytes, sms, s); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "launching the dump kernel");
     hc::Header h;

@@ -47,22 +47,17 @@ struct PhaseDesc {
 template <int KIND, int OP, int BB, int LB, int KPT>
 __device__ __forceinline__ void run_chunk(const BatchItemDev &it, long long k0, long long k1) {
     using T = Traits<KIND>;
-    constexpr int TILE = Shape<BB, LB, KPT>::TILE;
-    for (long long base = k0; base < k1; base += TILE) {
-        // keys past the chunk end belong to the next chunk: clamp n to it
-        if constexpr (OP == OP_INSERT)
-            insert_tile<KIND, BB, LB, KPT>(it.v, (const typename T::Key *)it.keys, (const typename T::Val *)it.vals,
-                                           k1, it.out, base, it.fold != 0);
-        else if constexpr (OP == OP_FIND)
-            find_tile<KIND, BB, LB, KPT>(it.v, (const typename T::Key *)it.keys, k1, it.out,
-                                         (typename T::Val *)it.vals_out, base);
-        else
-            erase_tile<KIND, BB, LB, KPT>(it.v, (const typename T::Key *)it.keys, k1, it.out, base, it.fold != 0);
-    }
+    constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
+    // keys past the chunk end belong to the next chunk: n is clamped to k1
+    Counts cnt;
+    run_tiles<KIND, BB, LB, KPT, OP>(it.v, (const typename T::Key *)it.keys, (const typename T::Val *)it.vals, nullptr,
+                                     it.out, (typename T::Val *)it.vals_out, k1, k0 / TILE, (k1 + TILE - 1) / TILE, 1,
+                                     it.fold != 0, cnt);
+    if constexpr (OP != OP_FIND) flush_counts(it.v, cnt);
 }
 
-// WIDE: one thread per key reading the item's whole bucket; otherwise 32-byte
-// lanes (bucket_bytes / 32 lanes per key).
+// WIDE: one thread per key reading the item's whole bucket (maps: keys and
+// values) or key region (sets); otherwise 32-byte lanes.
 template <int KIND, int OP, int WIDE, int KPT>
 __global__ void __launch_bounds__(256)
 k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_chunks, int tile,
@@ -83,10 +78,13 @@ k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_c
         const BatchItemDev it = items[lo];
         const long long k0 = ((long long)c - it.chunk_begin) * tile;
         const long long k1 = k0 + tile < it.n ? k0 + tile : it.n;
+        // wide: maps read the whole bucket (keys and values), sets the key region
+        constexpr bool M = Traits<KIND>::MAP;
+        constexpr int K32 = Slots<KIND, 32>::KRB, K64 = Slots<KIND, 64>::KRB, K128 = Slots<KIND, 128>::KRB;
         switch (it.bb) {
-            case 32: run_chunk<KIND, OP, 32, 32, KPT>(it, k0, k1); break;
-            case 64: run_chunk<KIND, OP, 64, WIDE ? 64 : 32, KPT>(it, k0, k1); break;
-            default: run_chunk<KIND, OP, 128, WIDE ? 128 : 32, KPT>(it, k0, k1); break;
+            case 32: run_chunk<KIND, OP, 32, WIDE ? (M ? 32 : K32) : (K32 < 32 ? K32 : 32), KPT>(it, k0, k1); break;
+            case 64: run_chunk<KIND, OP, 64, WIDE ? (M ? 64 : K64) : 32, KPT>(it, k0, k1); break;
+            default: run_chunk<KIND, OP, 128, WIDE ? (M ? 128 : K128) : 32, KPT>(it, k0, k1); break;
         }
     }
 }
@@ -452,6 +450,111 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
         e = cudaGetLastError();
         if (e != cudaSuccess) return bcuda(e, "launching a batch phase");
     }
+    return HC_OK;
+}
+
+}  // extern "C"
+
+// ---- dynamic batched launch with caller scratch ---------------------------
+// The served form forms a new batch at every dispatch.  Building a graph or
+// allocating descriptors per dispatch would cost more than small requests
+// themselves, so the caller hands in a device scratch buffer (one per stream
+// it dispatches on) that receives the descriptors and chunk counters.
+
+namespace {
+
+constexpr int kRunMaxItems = 4096;
+thread_local hc::BatchItemDev t_run_items[kRunMaxItems];
+
+}  // namespace
+
+extern "C" {
+
+HC_API int64_t hc_batch_scratch_bytes(int64_t n_items) {
+    if (n_items < 0 || n_items > kRunMaxItems) return -1;
+    return (int64_t)((n_items * sizeof(hc::BatchItemDev) + 255) / 256 * 256 + 256);
+}
+
+HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg, void *d_scratch,
+                          int64_t scratch_bytes, void *stream) {
+    if (n_items < 0 || (n_items > 0 && !items)) return bfail(HC_ERR_ARG, "bad item list");
+    if (n_items > kRunMaxItems)
+        return bfail(HC_ERR_ARG, "hc_batch_run takes at most 4096 items per call (got " +
+                                     std::to_string((long long)n_items) + ")");
+    if (n_items == 0) return HC_OK;
+    const int64_t need = hc_batch_scratch_bytes(n_items);
+    if (!d_scratch || scratch_bytes < need || reinterpret_cast<uintptr_t>(d_scratch) % 256)
+        return bfail(HC_ERR_ARG, "scratch must be 256-byte aligned and hold hc_batch_scratch_bytes(n_items) = " +
+                                     std::to_string((long long)need) + " bytes");
+    hc_batch_config c{};
+    if (cfg) c = *cfg;
+    const int lb = c.lane_bytes;
+    const int kpt = c.keys_per_group ? c.keys_per_group : 1;
+    const int block = c.block ? c.block : 256;
+    const int tile = c.tile ? c.tile : 4096;
+    if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole key region) or 32");
+    if (kpt != 1 && kpt != 2) return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
+    if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
+    if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
+
+    hc::PhaseDesc phases[12];
+    int n_phases = 0, n_dev = 0;
+    for (int op = 0; op < 3; ++op) {
+        for (int kind = 0; kind < 4; ++kind) {
+            hc::PhaseDesc ph{kind, op, n_dev, 0, 0, n_phases};
+            for (int64_t i = 0; i < n_items; ++i) {
+                const hc_batch_item &it = items[i];
+                if (!it.table || it.table->magic != HC_TABLE_MAGIC) return bfail(HC_ERR_ARG, "item with a bad table");
+                if (it.op < 0 || it.op > 2) return bfail(HC_ERR_ARG, "item with a bad op");
+                if (it.n < 0) return bfail(HC_ERR_ARG, "item with n < 0");
+                if (it.op != op || it.table->kind != kind || it.n == 0) continue;
+                const bool map = kind >= HC_MAP_I64_I32;
+                const int kb = kind == HC_SET_U32 ? 4 : 8;
+                if (!it.d_keys || reinterpret_cast<uintptr_t>(it.d_keys) % kb)
+                    return bfail(HC_ERR_ARG, "item keys NULL or misaligned");
+                if (op == HC_OP_INSERT && map && !it.d_vals) return bfail(HC_ERR_ARG, "insert item on a map without values");
+                if (op == HC_OP_FIND && !it.d_out) return bfail(HC_ERR_ARG, "find item without a found array");
+                hc::BatchItemDev &d = t_run_items[n_dev++];
+                d = hc::BatchItemDev{};
+                d.v = it.table->view;
+                d.keys = it.d_keys;
+                d.vals = map ? it.d_vals : nullptr;
+                d.out = it.d_out;
+                d.vals_out = map ? it.d_vals_out : nullptr;
+                d.n = it.n;
+                d.chunk_begin = ph.n_chunks;
+                d.bb = it.table->bucket_bytes;
+                d.fold = op == HC_OP_FIND ? 0 : it.table->shape[op].fold;
+                ph.n_chunks += (it.n + tile - 1) / tile;
+                ph.n_items++;
+            }
+            if (ph.n_items) phases[n_phases++] = ph;
+        }
+    }
+    if (n_phases == 0) return HC_OK;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return bcuda(e, "reading the device");
+    auto *d_items = static_cast<hc::BatchItemDev *>(d_scratch);
+    auto *d_ctr = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_scratch) + need - 256);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(d_items, t_run_items, (size_t)n_dev * sizeof(hc::BatchItemDev), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bcuda(e, "copying the batch descriptors");
+    hc::k_zero_counters<<<1, 32, 0, s>>>(d_ctr, n_phases);
+    for (int p = 0; p < n_phases; ++p) {
+        const hc::PhaseDesc &ph = phases[p];
+        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, lb, kpt);
+        int per_sm = c.blocks_per_sm;
+        if (per_sm <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0) != cudaSuccess) per_sm = 1;
+        if (per_sm <= 0) per_sm = 1;
+        long long g = (long long)sms * per_sm;
+        const long long want = (ph.n_chunks * 32 + block - 1) / block;
+        if (g > want) g = want;
+        k<<<(unsigned)(g > 0 ? g : 1), block, 0, s>>>(d_items + ph.item0, ph.n_items, ph.n_chunks, tile, d_ctr + ph.counter);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bcuda(e, "launching the batch phases");
     return HC_OK;
 }
 

@@ -1,25 +1,31 @@
 // hc_core.cuh -- device side of the GB300 hash containers.
 //
-// Layout.  A table holds `phys` slots in nb buckets of BB bytes of keys
-// (BB = 32, 64 or 128: one, two or four 32-byte sectors), followed, for maps,
-// by a parallel value array (structure of arrays):
-//   keys[phys]   uint32 (set<u32>) or 64-bit key bit patterns (other kinds)
-//   vals[phys]   int32 (map<i64,i32>) or uint64 (map<u64,u64>)
-// A probe reads key buckets only; a map reads one value when it has found
-// its key.  A key slot is EMPTY (all ones), a TOMBSTONE (all ones minus one)
-// or holds a key.  The two keys whose bit patterns equal those markers live
-// in two side slots of the header (every bit pattern is a valid key: the
-// paper avoids placeholder keys, Section 5.1).  Slots past the requested
-// capacity in the last bucket are padding: they hold TOMBSTONE and inserts
-// never claim them, so a table stores at most `capacity` keys in slots (fixed
-// capacity, Section 4).
+// Layout.  A table is nb buckets of BB bytes (32, 64 or 128), aligned to
+// their size, so a bucket is one, two or four 32-byte sectors inside one
+// 128-byte L2 line.  A bucket holds SPB slots as SPB keys followed, for maps,
+// by their SPB values:
+//   set<u32>       BB/4 keys          set<u64>  BB/8 keys
+//   map<u64,u64>   BB/16 keys + BB/16 values
+//   map<i64,i32>   the largest power of two of 12-byte slots that fits
+//                  (2, 4 or 8 keys + values, the rest padding)
+// On GB300 a random read of any size brings a whole 128-byte line from HBM
+// (3.83 DRAM sectors per random 32-byte read, for every load flavour), so the
+// cost of an operation is the number of lines it touches: keeping a key and
+// its value in one line makes a map lookup or insert touch one line.
+// A key slot is EMPTY (all ones), a TOMBSTONE (all ones minus one) or holds a
+// key.  The two keys whose bit patterns equal those markers live in two side
+// slots of the header (every bit pattern is a valid key: the paper avoids
+// placeholder keys, Section 5.1).  Slots past the requested capacity in the
+// last bucket are padding: they hold TOMBSTONE and inserts never claim them,
+// so a table stores at most `capacity` keys in slots (fixed capacity,
+// Section 4).
 //
 // Probing.  A key hashes to a first bucket; buckets are visited in order,
-// wrapping around, at most nb of them.  A group of G = BB / LB lanes reads one
-// bucket together (each lane LB = 32, 64 or 128 bytes with 32-byte vector
-// loads; G = 1 is one thread per key) and combines its findings with
-// __ballot_sync.  Each group may work on KPT keys at once, issuing all their
-// bucket loads before examining any.
+// wrapping around, at most nb of them.  A group of G = KRB / LB lanes reads the
+// bucket's key region (KRB bytes) together, each lane LB bytes (16, 32, 64
+// or 128) with vector loads; G = 1 is one thread per key.  The lanes combine
+// their findings with __ballot_sync.  Each group may work on KPT keys at once,
+// issuing all their bucket loads before examining any.
 //
 //   insert: stop at the key (EXISTS) or at the first bucket holding an EMPTY
 //           slot; claim the first free slot (EMPTY or TOMBSTONE, not padding)
@@ -69,8 +75,7 @@ static_assert(sizeof(Header) == 256, "header is one 256-byte block");
 // What a kernel needs to reach a table; passed by value (Section 3.7: a
 // shallow copy of a device object can be handed to kernels).
 struct View {
-    unsigned char *keys;         // nb * BB bytes
-    unsigned char *vals;         // phys values (maps), else null
+    unsigned char *buckets;      // nb * BB bytes
     Header *hdr;
     unsigned long long nb;       // buckets
     unsigned long long seed;
@@ -145,14 +150,18 @@ __device__ __forceinline__ unsigned long long next_bucket(const View &v, unsigne
 // only (the slots are shared by all SMs and modified by atomics; an L1 copy
 // could be stale after a lost compare-and-swap).
 template <int LB> struct LaneWords {
-    static_assert(LB == 32 || LB == 64 || LB == 128, "lane bytes");
+    static_assert(LB == 16 || LB == 32 || LB == 64 || LB == 128, "lane bytes");
     unsigned long long w[LB / 8];
     __device__ __forceinline__ void load(const unsigned char *p) {
+        if constexpr (LB == 16) {
+            asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(p));
+        } else {
 #pragma unroll
-        for (int q = 0; q < LB / 32; ++q)
-            asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
-                         : "=l"(w[4 * q]), "=l"(w[4 * q + 1]), "=l"(w[4 * q + 2]), "=l"(w[4 * q + 3])
-                         : "l"(p + 32 * q));
+            for (int q = 0; q < LB / 32; ++q)
+                asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+                             : "=l"(w[4 * q]), "=l"(w[4 * q + 1]), "=l"(w[4 * q + 2]), "=l"(w[4 * q + 3])
+                             : "l"(p + 32 * q));
+        }
     }
 };
 
@@ -173,16 +182,34 @@ __device__ __forceinline__ typename Traits<KIND>::Key cas_key(unsigned char *slo
         return atomicCAS(reinterpret_cast<unsigned long long *>(slot), expect, desired);
 }
 
-template <int KIND>
-__device__ __forceinline__ void store_val(const View &v, unsigned long long idx, unsigned long long val) {
+// Where slot s of bucket b keeps its key and value (see the layout above).
+template <int KIND, int BB> struct Slots {
     using T = Traits<KIND>;
-    if constexpr (T::MAP) reinterpret_cast<typename T::Val *>(v.vals)[idx] = (typename T::Val)val;
+    static constexpr int KB = (int)sizeof(typename T::Key);
+    static constexpr int VB = T::MAP ? (int)sizeof(typename T::Val) : 0;
+    static constexpr int fit(int n) { return n >= 16 ? 16 : n >= 8 ? 8 : n >= 4 ? 4 : n >= 2 ? 2 : 1; }
+    static constexpr int SPB = T::MAP ? fit(BB / (KB + VB)) : BB / KB;   // slots per bucket
+    static constexpr int KRB = SPB * KB;                                 // key region bytes
+    static_assert(KRB + SPB * VB <= BB, "bucket overflow");
+    __device__ __forceinline__ static unsigned char *key(const View &v, unsigned long long b, int s) {
+        return v.buckets + b * BB + (size_t)s * KB;
+    }
+    __device__ __forceinline__ static unsigned char *val(const View &v, unsigned long long b, int s) {
+        return v.buckets + b * BB + KRB + (size_t)s * VB;
+    }
+};
+
+template <int KIND, int BB>
+__device__ __forceinline__ void store_val(const View &v, unsigned long long b, int s, unsigned long long val) {
+    using T = Traits<KIND>;
+    if constexpr (T::MAP) *reinterpret_cast<typename T::Val *>(Slots<KIND, BB>::val(v, b, s)) = (typename T::Val)val;
 }
 
-template <int KIND>
-__device__ __forceinline__ unsigned long long load_val(const View &v, unsigned long long idx) {
+template <int KIND, int BB>
+__device__ __forceinline__ unsigned long long load_val(const View &v, unsigned long long b, int s) {
     using T = Traits<KIND>;
-    if constexpr (T::MAP) return (unsigned long long)__ldcg(reinterpret_cast<const typename T::Val *>(v.vals) + idx);
+    if constexpr (T::MAP)
+        return (unsigned long long)__ldcg(reinterpret_cast<const typename T::Val *>(Slots<KIND, BB>::val(v, b, s)));
     else return 0ull;
 }
 
@@ -217,20 +244,35 @@ template <int G> struct Group {
     }
 };
 
-// Keys handled by a warp per tile: (32 / G) groups of KPT keys.
-template <int BB, int LB, int KPT> struct Shape {
-    static constexpr int G = BB / LB;
-    static constexpr int GROUPS = 32 / G;
-    static constexpr int TILE = GROUPS * KPT;
+// Slot-layout constants of a (kind, bucket, lane) combination.
+// FULL (maps, LB == BB): one thread reads the whole bucket, keys and values,
+// so a lookup that finds its key has the value without a second load.
+template <int KIND, int BB, int LB> struct Layout {
+    using S = Slots<KIND, BB>;
+    static constexpr int KB = S::KB;
+    static constexpr int SPB = S::SPB;                       // slots per bucket
+    static constexpr bool FULL = Traits<KIND>::MAP && LB == BB;
+    static constexpr int G = FULL ? 1 : S::KRB / LB;         // lanes per key
+    static constexpr int SPL = FULL ? SPB : LB / KB;         // key slots per lane (<= 32)
+    static constexpr uint32_t ALL = SPL == 32 ? 0xffffffffu : ((1u << SPL) - 1u);
+    static_assert(FULL || (LB <= S::KRB && S::KRB % LB == 0), "lane bytes must divide the key region");
+    static_assert(SPL <= 32, "lane masks are 32 bits");
 };
 
-// Slot-layout constants of a (kind, bucket, lane) combination.
-template <int KIND, int BB, int LB> struct Layout {
-    static constexpr int KB = (int)sizeof(typename Traits<KIND>::Key);
-    static constexpr int SPL = LB / KB;   // key slots per lane (<= 32)
-    static constexpr int SPB = BB / KB;   // key slots per bucket
-    static constexpr uint32_t ALL = SPL == 32 ? 0xffffffffu : ((1u << SPL) - 1u);
-    static_assert(SPL <= 32, "lane masks are 32 bits");
+// Value of slot s from a FULL lane's words (values follow the KRB key bytes).
+template <int KIND, int BB, int LB>
+__device__ __forceinline__ unsigned long long word_val(const LaneWords<LB> &lw, int s) {
+    using T = Traits<KIND>;
+    constexpr int KRB = Slots<KIND, BB>::KRB;
+    if constexpr (sizeof(typename T::Val) == 8) return lw.w[KRB / 8 + s];
+    else return (uint32_t)(lw.w[(KRB + 4 * s) / 8] >> (((KRB + 4 * s) % 8) * 8));
+}
+
+// Keys handled by a warp per tile: (32 / G) groups of KPT keys.
+template <int KIND, int BB, int LB, int KPT> struct Shape {
+    static constexpr int G = Layout<KIND, BB, LB>::G;
+    static constexpr int GROUPS = 32 / G;
+    static constexpr int TILE = GROUPS * KPT;
 };
 
 // Load the KPT keys of this group (tile position `first`), vectorised when the
@@ -325,7 +367,7 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Lay = Layout<KIND, BB, LB>;
-    constexpr int G = BB / LB;
+    constexpr int G = Lay::G;
     constexpr int SPL = Lay::SPL;
     const Group<G> grp;
 
@@ -346,7 +388,7 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.keys + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(v.buckets + b[j] * BB + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;
@@ -397,9 +439,8 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
             const Key expect = ff_empty[j] ? T::EMPTY : T::TOMB;
             Key old = expect;
             if (grp.sub == owner) {
-                const unsigned long long idx = ffb[j] * Lay::SPB + ffs_slot[j];
-                old = cas_key<KIND>(v.keys + idx * Lay::KB, expect, k[j]);
-                if (old == expect) store_val<KIND>(v, idx, val[j]);
+                old = cas_key<KIND>(Slots<KIND, BB>::key(v, ffb[j], ffs_slot[j]), expect, k[j]);
+                if (old == expect) store_val<KIND, BB>(v, ffb[j], ffs_slot[j], val[j]);
             }
             old = grp.bcast(old, owner);
             if (old == expect) {
@@ -433,7 +474,7 @@ __device__ __forceinline__ void find_group(const View &v, const typename Traits<
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Lay = Layout<KIND, BB, LB>;
-    constexpr int G = BB / LB;
+    constexpr int G = Lay::G;
     constexpr int SPL = Lay::SPL;
     const Group<G> grp;
 
@@ -449,7 +490,7 @@ __device__ __forceinline__ void find_group(const View &v, const typename Traits<
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.keys + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(v.buckets + b[j] * BB + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;
@@ -465,7 +506,8 @@ __device__ __forceinline__ void find_group(const View &v, const typename Traits<
                 const int owner = __ffs(gm) - 1;
                 unsigned long long val = 0;
                 if constexpr (T::MAP) {
-                    if (grp.sub == owner) val = load_val<KIND>(v, b[j] * Lay::SPB + owner * SPL + (__ffs(lm) - 1));
+                    if constexpr (Lay::FULL) val = word_val<KIND, BB, LB>(lw[j], __ffs(lm) - 1);
+                    else if (grp.sub == owner) val = load_val<KIND, BB>(v, b[j], owner * SPL + (__ffs(lm) - 1));
                     val = grp.bcast(val, owner);
                 }
                 res.st[j] = 1;
@@ -490,7 +532,7 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Lay = Layout<KIND, BB, LB>;
-    constexpr int G = BB / LB;
+    constexpr int G = Lay::G;
     constexpr int SPL = Lay::SPL;
     const Group<G> grp;
 
@@ -506,7 +548,7 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.keys + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(v.buckets + b[j] * BB + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;
@@ -521,10 +563,8 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
             if (gm) {
                 const int owner = __ffs(gm) - 1;
                 Key old = T::TOMB;
-                if (grp.sub == owner) {
-                    const unsigned long long idx = b[j] * Lay::SPB + owner * SPL + (__ffs(lm) - 1);
-                    old = cas_key<KIND>(v.keys + idx * Lay::KB, k[j], T::TOMB);
-                }
+                if (grp.sub == owner)
+                    old = cas_key<KIND>(Slots<KIND, BB>::key(v, b[j], owner * SPL + (__ffs(lm) - 1)), k[j], T::TOMB);
                 old = grp.bcast(old, owner);
                 // a failed swap means an equal key in this batch erased it first
                 res.st[j] = old == k[j] ? ST_ERASED : ST_NOT_FOUND;
@@ -541,39 +581,75 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
 }
 
 // ------------------------------------------------------------ warp tiles ---
-// One warp processes keys [tile_base, tile_base + TILE) of a call.  These are
-// shared by the one-launch-per-call kernels and the batched persistent kernel.
+// One warp processes keys [tile_base, tile_base + TILE) of a call.  The keys
+// (and values, skip flags) of a tile are loaded into a TileIn first, so a
+// persistent kernel can load the next tile while the current one probes.
+// These are shared by the range kernels and the batched persistent kernel.
 
 template <class V> __device__ __forceinline__ unsigned long long widen(V x) { return (unsigned long long)x; }
 
-template <int KIND, int BB, int LB, int KPT>
-__device__ __forceinline__ void insert_tile(const View &v, const typename Traits<KIND>::Key *keys,
-                                            const typename Traits<KIND>::Val *vals, long long n, uint8_t *status,
-                                            long long tile_base, bool fold, const uint8_t *skip = nullptr) {
-    using T = Traits<KIND>;
-    using Key = typename T::Key;
-    using S = Shape<BB, LB, KPT>;
-    const int lane = threadIdx.x & 31;
-    const long long first = tile_base + (long long)(lane / S::G) * KPT;
-    const bool lead_lane = (lane & (S::G - 1)) == 0;
+template <int KIND, int KPT> struct TileIn {
+    typename Traits<KIND>::Key k[KPT];
+    unsigned long long val[KPT];
+    uint32_t valid;     // keys inside [0, n)
+    uint32_t present;   // keys a preceding find reported as stored (skip flags)
+};
 
-    Key k[KPT];
-    uint32_t valid;
-    load_keys<KPT>(keys, first, n, k, valid);
-    // keys a preceding find reported as stored are EXISTS without a probe
-    uint32_t present = 0;
+// First key index of this lane's group in a tile.
+template <int KIND, int BB, int LB, int KPT>
+__device__ __forceinline__ long long group_first(long long tile_base) {
+    return tile_base + (long long)((threadIdx.x & 31) / Shape<KIND, BB, LB, KPT>::G) * KPT;
+}
+
+template <int KIND, int KPT>
+__device__ __forceinline__ void load_tile(TileIn<KIND, KPT> &in, const typename Traits<KIND>::Key *keys,
+                                          const typename Traits<KIND>::Val *vals, const uint8_t *skip, long long first,
+                                          long long n) {
+    using T = Traits<KIND>;
+    load_keys<KPT>(keys, first, n, in.k, in.valid);
+    in.present = 0;
     if (skip) {
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if ((valid >> j & 1u) && ld_stream(skip + first + j)) present |= 1u << j;
+            if ((in.valid >> j & 1u) && ld_stream(skip + first + j)) in.present |= 1u << j;
     }
-    unsigned long long val[KPT];
 #pragma unroll
     for (int j = 0; j < KPT; ++j)
-        val[j] = (T::MAP && (valid >> j & 1u) && !(present >> j & 1u)) ? widen(ld_stream(vals + first + j)) : 0ull;
+        in.val[j] = (T::MAP && vals && (in.valid >> j & 1u) && !(in.present >> j & 1u))
+                        ? widen(ld_stream(vals + first + j)) : 0ull;
+}
+
+// Per-thread counts of an insert or erase, added to the header by flush_counts.
+struct Counts {
+    uint32_t ins = 0, new_slot = 0, del = 0, over = 0;
+};
+
+// One atomic per warp per counter.  All 32 lanes must call it.
+__device__ __forceinline__ void flush_counts(const View &v, Counts &c) {
+    __syncwarp();
+    const uint32_t w_ins = __reduce_add_sync(0xffffffffu, c.ins);
+    const uint32_t w_new = __reduce_add_sync(0xffffffffu, c.new_slot);
+    const uint32_t w_del = __reduce_add_sync(0xffffffffu, c.del);
+    const uint32_t w_over = __reduce_or_sync(0xffffffffu, c.over);
+    if ((threadIdx.x & 31) == 0) {
+        const long long d = (long long)w_ins - (long long)w_del;
+        if (d) atomicAdd(&v.hdr->live, (unsigned long long)d);
+        if (w_new) atomicAdd(&v.hdr->used, (unsigned long long)w_new);
+        if (w_over) atomicOr(&v.hdr->err, ERR_OVERFLOW);
+    }
+    c = Counts();
+}
+
+template <int KIND, int BB, int LB, int KPT>
+__device__ __forceinline__ void insert_tile(const View &v, const TileIn<KIND, KPT> &in, long long first,
+                                            uint8_t *status, bool fold, Counts &cnt) {
+    using T = Traits<KIND>;
+    using S = Shape<KIND, BB, LB, KPT>;
+    const int lane = threadIdx.x & 31;
+    const bool lead_lane = (lane & (S::G - 1)) == 0;
 
     int leader[KPT];
-    if (fold) fold_duplicates<KIND, S::G, KPT>(k, valid, leader);
+    if (fold) fold_duplicates<KIND, S::G, KPT>(in.k, in.valid, leader);
     else {
 #pragma unroll
         for (int j = 0; j < KPT; ++j) leader[j] = -1;
@@ -584,13 +660,13 @@ __device__ __forceinline__ void insert_tile(const View &v, const typename Traits
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
         res.st[j] = ST_EXISTS;
-        if (!(valid >> j & 1u) || leader[j] >= 0 || (present >> j & 1u)) continue;
-        const int side = side_index<KIND>(k[j]);
+        if (!(in.valid >> j & 1u) || leader[j] >= 0 || (in.present >> j & 1u)) continue;
+        const int side = side_index<KIND>(in.k[j]);
         if (side >= 0) {                         // key equal to a marker: side slot
             uint32_t won = 0;
             if (lead_lane) {
                 won = atomicCAS(&v.hdr->side_present[side], 0u, 1u) == 0u;
-                if (won) v.hdr->side_val[side] = val[j];
+                if (won) v.hdr->side_val[side] = in.val[j];
                 n_ins += won;
             }
             res.st[j] = Group<S::G>().bcast(won, 0) ? ST_INSERTED : ST_EXISTS;
@@ -598,7 +674,7 @@ __device__ __forceinline__ void insert_tile(const View &v, const typename Traits
         }
         todo |= 1u << j;
     }
-    insert_group<KIND, BB, LB, KPT>(v, k, val, todo, res, n_ins, n_new);
+    insert_group<KIND, BB, LB, KPT>(v, in.k, in.val, todo, res, n_ins, n_new);
 
     if (fold) {
         __syncwarp();
@@ -608,47 +684,32 @@ __device__ __forceinline__ void insert_tile(const View &v, const typename Traits
             if (leader[j] >= 0) res.st[j] = ls == ST_OVERFLOW ? ST_OVERFLOW : ST_EXISTS;
         }
     }
-    uint32_t over = 0;
     if (lead_lane) {
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
-            if (!(valid >> j & 1u)) continue;
-            over |= res.st[j] == ST_OVERFLOW;
+            if (!(in.valid >> j & 1u)) continue;
+            cnt.over |= res.st[j] == ST_OVERFLOW;
             if (status) st_stream(status + first + j, (uint8_t)res.st[j]);
         }
     }
-    __syncwarp();
-    const uint32_t w_ins = __reduce_add_sync(0xffffffffu, n_ins);
-    const uint32_t w_new = __reduce_add_sync(0xffffffffu, n_new);
-    const uint32_t w_over = __reduce_or_sync(0xffffffffu, over);
-    if (lane == 0) {
-        if (w_ins) atomicAdd(&v.hdr->live, (unsigned long long)w_ins);
-        if (w_new) atomicAdd(&v.hdr->used, (unsigned long long)w_new);
-        if (w_over) atomicOr(&v.hdr->err, ERR_OVERFLOW);
-    }
+    cnt.ins += n_ins;
+    cnt.new_slot += n_new;
 }
 
 template <int KIND, int BB, int LB, int KPT>
-__device__ __forceinline__ void find_tile(const View &v, const typename Traits<KIND>::Key *keys, long long n,
-                                          uint8_t *found, typename Traits<KIND>::Val *vals_out, long long tile_base) {
+__device__ __forceinline__ void find_tile(const View &v, const TileIn<KIND, KPT> &in, long long first, uint8_t *found,
+                                          typename Traits<KIND>::Val *vals_out) {
     using T = Traits<KIND>;
-    using Key = typename T::Key;
-    using S = Shape<BB, LB, KPT>;
-    const int lane = threadIdx.x & 31;
-    const long long first = tile_base + (long long)(lane / S::G) * KPT;
-    const bool lead_lane = (lane & (S::G - 1)) == 0;
-
-    Key k[KPT];
-    uint32_t valid;
-    load_keys<KPT>(keys, first, n, k, valid);
+    using S = Shape<KIND, BB, LB, KPT>;
+    const bool lead_lane = ((threadIdx.x & 31) & (S::G - 1)) == 0;
     TileResult<KPT> res;
     uint32_t todo = 0;
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
         res.st[j] = 0;
         res.val[j] = 0;
-        if (!(valid >> j & 1u)) continue;
-        const int side = side_index<KIND>(k[j]);
+        if (!(in.valid >> j & 1u)) continue;
+        const int side = side_index<KIND>(in.k[j]);
         if (side >= 0) {
             res.st[j] = *((volatile unsigned int *)&v.hdr->side_present[side]) ? 1u : 0u;
             res.val[j] = res.st[j] ? *((volatile unsigned long long *)&v.hdr->side_val[side]) : 0ull;
@@ -656,11 +717,11 @@ __device__ __forceinline__ void find_tile(const View &v, const typename Traits<K
         }
         todo |= 1u << j;
     }
-    find_group<KIND, BB, LB, KPT>(v, k, todo, res);
+    find_group<KIND, BB, LB, KPT>(v, in.k, todo, res);
     if (lead_lane) {
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
-            if (!(valid >> j & 1u)) continue;
+            if (!(in.valid >> j & 1u)) continue;
             if (found) st_stream(found + first + j, (uint8_t)res.st[j]);
             if constexpr (T::MAP) {
                 if (vals_out) st_stream(vals_out + first + j, (typename T::Val)res.val[j]);
@@ -670,20 +731,12 @@ __device__ __forceinline__ void find_tile(const View &v, const typename Traits<K
 }
 
 template <int KIND, int BB, int LB, int KPT>
-__device__ __forceinline__ void erase_tile(const View &v, const typename Traits<KIND>::Key *keys, long long n,
-                                           uint8_t *status, long long tile_base, bool fold) {
-    using T = Traits<KIND>;
-    using Key = typename T::Key;
-    using S = Shape<BB, LB, KPT>;
-    const int lane = threadIdx.x & 31;
-    const long long first = tile_base + (long long)(lane / S::G) * KPT;
-    const bool lead_lane = (lane & (S::G - 1)) == 0;
-
-    Key k[KPT];
-    uint32_t valid;
-    load_keys<KPT>(keys, first, n, k, valid);
+__device__ __forceinline__ void erase_tile(const View &v, const TileIn<KIND, KPT> &in, long long first,
+                                           uint8_t *status, bool fold, Counts &cnt) {
+    using S = Shape<KIND, BB, LB, KPT>;
+    const bool lead_lane = ((threadIdx.x & 31) & (S::G - 1)) == 0;
     int leader[KPT];
-    if (fold) fold_duplicates<KIND, S::G, KPT>(k, valid, leader);
+    if (fold) fold_duplicates<KIND, S::G, KPT>(in.k, in.valid, leader);
     else {
 #pragma unroll
         for (int j = 0; j < KPT; ++j) leader[j] = -1;
@@ -693,8 +746,8 @@ __device__ __forceinline__ void erase_tile(const View &v, const typename Traits<
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
         res.st[j] = ST_NOT_FOUND;
-        if (!(valid >> j & 1u) || leader[j] >= 0) continue;
-        const int side = side_index<KIND>(k[j]);
+        if (!(in.valid >> j & 1u) || leader[j] >= 0) continue;
+        const int side = side_index<KIND>(in.k[j]);
         if (side >= 0) {
             uint32_t won = 0;
             if (lead_lane) {
@@ -706,15 +759,39 @@ __device__ __forceinline__ void erase_tile(const View &v, const typename Traits<
         }
         todo |= 1u << j;
     }
-    erase_group<KIND, BB, LB, KPT>(v, k, todo, res, n_del);
+    erase_group<KIND, BB, LB, KPT>(v, in.k, todo, res, n_del);
     if (lead_lane && status) {
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (valid >> j & 1u) st_stream(status + first + j, (uint8_t)res.st[j]);
+            if (in.valid >> j & 1u) st_stream(status + first + j, (uint8_t)res.st[j]);
     }
-    __syncwarp();
-    const uint32_t w_del = __reduce_add_sync(0xffffffffu, n_del);
-    if (lane == 0 && w_del) atomicAdd(&v.hdr->live, (unsigned long long)(-(long long)w_del));
+    cnt.del += n_del;
+}
+
+// The keys [k0, k1) of one call processed by one warp, tile after tile, with
+// the next tile's inputs loaded before the current tile probes.  Used by the
+// range kernels (one warp-strided sweep over the call) and by the batched
+// kernel (one chunk).  OP: 0 insert, 1 find, 2 erase.
+template <int KIND, int BB, int LB, int KPT, int OP>
+__device__ __forceinline__ void run_tiles(const View &v, const typename Traits<KIND>::Key *keys,
+                                          const typename Traits<KIND>::Val *vals, const uint8_t *skip, uint8_t *out,
+                                          typename Traits<KIND>::Val *vals_out, long long n, long long t0,
+                                          long long t_end, long long t_step, bool fold, Counts &cnt) {
+    constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
+    if (t0 >= t_end) return;
+    TileIn<KIND, KPT> cur, nxt;
+    long long first = group_first<KIND, BB, LB, KPT>(t0 * TILE);
+    load_tile<KIND, KPT>(cur, keys, OP == 0 ? vals : nullptr, OP == 0 ? skip : nullptr, first, n);
+    for (long long t = t0; t < t_end; t += t_step) {
+        const long long tn = t + t_step;
+        const long long first_n = group_first<KIND, BB, LB, KPT>(tn * TILE);
+        if (tn < t_end) load_tile<KIND, KPT>(nxt, keys, OP == 0 ? vals : nullptr, OP == 0 ? skip : nullptr, first_n, n);
+        if constexpr (OP == 0) insert_tile<KIND, BB, LB, KPT>(v, cur, first, out, fold, cnt);
+        else if constexpr (OP == 1) find_tile<KIND, BB, LB, KPT>(v, cur, first, out, vals_out);
+        else erase_tile<KIND, BB, LB, KPT>(v, cur, first, out, fold, cnt);
+        cur = nxt;
+        first = first_n;
+    }
 }
 
 }  // namespace hc

@@ -14,20 +14,21 @@ struct Header;
 enum : int { OP_INSERT = 0, OP_FIND = 1, OP_ERASE = 2 };
 
 struct LaunchShape {
-    int lane_bytes;       // 16 or 32
-    int keys_per_group;   // 1, 2, 4
+    int lane_bytes;       // 16 (maps), 32, 64 or 128
+    int keys_per_group;   // 1 or 2
     int block;            // threads per block
     int fold;             // 1 = fold equal keys inside a warp
+    int sms;              // multiprocessors of the table's device (grid sizing)
 };
 
 #define HC_DECLARE_KIND(NAME)                                                                                       \
     cudaError_t NAME##_range(int op, const View &v, int bb, const void *keys, const void *vals, long long n,        \
                              uint8_t *out, void *vals_out, const LaunchShape &sh, const uint8_t *skip,              \
                              cudaStream_t s);                                                                       \
-    cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int sms,               \
+    cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int bb, int sms,       \
                              cudaStream_t s);                                                                       \
     cudaError_t NAME##_dump(const View &v, unsigned long long phys, void *ko, void *vo, unsigned long long cap,     \
-                            int sms, cudaStream_t s);                                                               \
+                            int bb, int sms, cudaStream_t s);                                                       \
     cudaError_t NAME##_rehash(const View &ov, unsigned long long ophys, const View &nv, int bb, int sms,            \
                               cudaStream_t s);
 

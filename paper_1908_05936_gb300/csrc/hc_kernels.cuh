@@ -9,34 +9,53 @@
 namespace hc {
 
 // ------------------------------------------------------- range kernels ---
+// One tile per warp and as many blocks as the call needs: short-lived warps
+// let the block scheduler refill an SM as soon as its slowest probes finish.
+// (A persistent grid-stride form that prefetched the next tile measured
+// 1.3-2x slower on GB300 for every shape.)
 
 template <int KIND, int BB, int LB, int KPT>
 __global__ void __launch_bounds__(512)
 k_insert(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
          uint8_t *status, int fold, const uint8_t *skip) {
+    constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    insert_tile<KIND, BB, LB, KPT>(v, keys, vals, n, status, warp * Shape<BB, LB, KPT>::TILE, fold != 0, skip);
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    Counts cnt;
+    run_tiles<KIND, BB, LB, KPT, 0>(v, keys, vals, skip, status, nullptr, n, warp, (n + TILE - 1) / TILE, warps,
+                                    fold != 0, cnt);
+    flush_counts(v, cnt);
 }
 
 template <int KIND, int BB, int LB, int KPT>
 __global__ void __launch_bounds__(512)
 k_find(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *found,
        typename Traits<KIND>::Val *vals_out) {
+    constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    find_tile<KIND, BB, LB, KPT>(v, keys, n, found, vals_out, warp * Shape<BB, LB, KPT>::TILE);
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    Counts cnt;
+    run_tiles<KIND, BB, LB, KPT, 1>(v, keys, nullptr, nullptr, found, vals_out, n, warp, (n + TILE - 1) / TILE, warps,
+                                    false, cnt);
 }
 
 template <int KIND, int BB, int LB, int KPT>
 __global__ void __launch_bounds__(512)
 k_erase(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status, int fold) {
+    constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    erase_tile<KIND, BB, LB, KPT>(v, keys, n, status, warp * Shape<BB, LB, KPT>::TILE, fold != 0);
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    Counts cnt;
+    run_tiles<KIND, BB, LB, KPT, 2>(v, keys, nullptr, nullptr, status, nullptr, n, warp, (n + TILE - 1) / TILE, warps,
+                                    fold != 0, cnt);
+    flush_counts(v, cnt);
 }
 
 // ---------------------------------------------------------------- clear ---
-// Every key slot EMPTY (all-ones bytes, 32-byte stores), the header zeroed;
-// then the padding slots of the last bucket become tombstones.  Values need no
-// initialisation: a value is read only after its key was found.
+// Every bucket all-ones bytes (so every key slot is EMPTY; values need no
+// initialisation, a value is read only after its key was found), 32-byte
+// stores; the header zeroed; then the padding slots of the last bucket become
+// tombstones.
 
 static __global__ void __launch_bounds__(256)
 k_fill_empty(unsigned char *keys, unsigned long long bytes, Header *hdr) {
@@ -50,30 +69,37 @@ k_fill_empty(unsigned char *keys, unsigned long long bytes, Header *hdr) {
         reinterpret_cast<unsigned long long *>(hdr)[threadIdx.x] = 0ull;
 }
 
-template <int KIND>
-__global__ void k_pad_tombstones(unsigned char *keys, unsigned long long first, unsigned long long count) {
+template <int KIND, int BB>
+__global__ void k_pad_tombstones(View v, unsigned long long first, unsigned long long count) {
     using T = Traits<KIND>;
+    using S = Slots<KIND, BB>;
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) reinterpret_cast<typename T::Key *>(keys)[first + i] = T::TOMB;
+    if (i < count) {
+        const unsigned long long slot = first + i;
+        *reinterpret_cast<typename T::Key *>(S::key(v, slot / S::SPB, (int)(slot % S::SPB))) = T::TOMB;
+    }
 }
 
 // ----------------------------------------------------------------- dump ---
 // Stored (key, value) pairs appended to the output through one atomic add per
 // warp on the header's cursor.
 
-template <int KIND>
+template <int KIND, int BB>
 __global__ void __launch_bounds__(256)
 k_dump(View v, unsigned long long phys, typename Traits<KIND>::Key *keys_out, typename Traits<KIND>::Val *vals_out,
        unsigned long long cap) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
+    using S = Slots<KIND, BB>;
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     // whole-warp steps so that every lane reaches the shuffles
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
          base < phys; base += stride) {
         const unsigned long long i = base + lane;
-        const Key key = i < phys ? reinterpret_cast<const Key *>(v.keys)[i] : T::EMPTY;
+        const unsigned long long b = i / S::SPB;
+        const int sl = (int)(i % S::SPB);
+        const Key key = i < phys ? *reinterpret_cast<const Key *>(S::key(v, b, sl)) : T::EMPTY;
         const bool live = key != T::EMPTY && key != T::TOMB;
         const unsigned m = __ballot_sync(0xffffffffu, live);
         if (!m) continue;
@@ -85,7 +111,7 @@ k_dump(View v, unsigned long long phys, typename Traits<KIND>::Key *keys_out, ty
             if (pos < cap) {
                 keys_out[pos] = key;
                 if constexpr (T::MAP) {
-                    if (vals_out) vals_out[pos] = reinterpret_cast<const typename T::Val *>(v.vals)[i];
+                    if (vals_out) vals_out[pos] = *reinterpret_cast<const typename T::Val *>(S::val(v, b, sl));
                 }
             }
         }
@@ -114,21 +140,24 @@ __global__ void __launch_bounds__(256)
 k_rehash(View old_v, unsigned long long old_phys, View new_v) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
-    constexpr int SPB = BB / (int)sizeof(Key);
+    using S = Slots<KIND, BB>;
+    constexpr int SPB = S::SPB;
     uint32_t moved = 0;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
          base < old_phys; base += stride) {
         const unsigned long long i = base + (threadIdx.x & 31);
         if (i >= old_phys) continue;
-        const Key key = reinterpret_cast<const Key *>(old_v.keys)[i];
+        const unsigned long long ob = i / SPB;
+        const int os = (int)(i % SPB);
+        const Key key = *reinterpret_cast<const Key *>(S::key(old_v, ob, os));
         if (key == T::EMPTY || key == T::TOMB) continue;
         unsigned long long val = 0;
-        if constexpr (T::MAP) val = reinterpret_cast<const typename T::Val *>(old_v.vals)[i];
+        if constexpr (T::MAP) val = *reinterpret_cast<const typename T::Val *>(S::val(old_v, ob, os));
         unsigned long long b = first_bucket(new_v, (unsigned long long)key);
         bool done = false;
         for (unsigned long long p = 0; p < new_v.nb && !done;) {
-            Key *bucket = reinterpret_cast<Key *>(new_v.keys + b * BB);
+            Key *bucket = reinterpret_cast<Key *>(S::key(new_v, b, 0));
             int s = 0;
             for (; s < SPB; ++s) {
                 Key ks;
@@ -142,7 +171,7 @@ k_rehash(View old_v, unsigned long long old_phys, View new_v) {
                 continue;
             }
             if (cas_key<KIND>(reinterpret_cast<unsigned char *>(bucket + s), T::EMPTY, key) == T::EMPTY) {
-                store_val<KIND>(new_v, b * SPB + s, val);
+                store_val<KIND, BB>(new_v, b, s, val);
                 done = true;
             }
             // a lost race re-reads the same bucket
@@ -157,26 +186,26 @@ k_rehash(View old_v, unsigned long long old_phys, View new_v) {
 // ------------------------------------------------------------ launchers ---
 
 inline unsigned grid_for(long long n, int tile, int block) {
-    const long long warps = (n + tile - 1) / tile;
-    const long long threads = warps * 32;
-    return (unsigned)((threads + block - 1) / block);
+    const long long warps = (n + tile - 1) / tile;                // one tile per warp
+    return (unsigned)((warps * 32 + block - 1) / block);
 }
 
 template <int KIND, int BB, int LB, int KPT>
 cudaError_t launch_range_shape(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
-                               void *vals_out, int block, int fold, const uint8_t *skip, cudaStream_t s) {
+                               void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Val = typename T::Val;
-    constexpr int TILE = Shape<BB, LB, KPT>::TILE;
+    constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
+    const int block = sh.block;
+    if (n <= 0) return cudaSuccess;
     const unsigned grid = grid_for(n, TILE, block);
-    if (grid == 0) return cudaSuccess;
     if (op == OP_INSERT)
-        k_insert<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, (const Val *)vals, n, out, fold, skip);
+        k_insert<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, (const Val *)vals, n, out, sh.fold, skip);
     else if (op == OP_FIND)
         k_find<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, n, out, (Val *)vals_out);
     else
-        k_erase<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, n, out, fold);
+        k_erase<KIND, BB, LB, KPT><<<grid, block, 0, s>>>(v, (const Key *)keys, n, out, sh.fold);
     return cudaGetLastError();
 }
 
@@ -184,8 +213,8 @@ template <int KIND, int BB, int LB>
 cudaError_t launch_range_kpt(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
                              void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
     switch (sh.keys_per_group) {
-        case 1: return launch_range_shape<KIND, BB, LB, 1>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, skip, s);
-        case 2: return launch_range_shape<KIND, BB, LB, 2>(op, v, keys, vals, n, out, vals_out, sh.block, sh.fold, skip, s);
+        case 1: return launch_range_shape<KIND, BB, LB, 1>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+        case 2: return launch_range_shape<KIND, BB, LB, 2>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -193,11 +222,18 @@ cudaError_t launch_range_kpt(int op, const View &v, const void *keys, const void
 template <int KIND, int BB>
 cudaError_t launch_range_lb(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
                             void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
-    if (sh.lane_bytes == 32) return launch_range_kpt<KIND, BB, 32>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
-    if constexpr (BB >= 64)
+    constexpr int KRB = Slots<KIND, BB>::KRB;
+    if constexpr (Traits<KIND>::MAP) {
+        if (sh.lane_bytes == 16) return launch_range_kpt<KIND, BB, 16>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+    }
+    if constexpr (KRB >= 32)
+        if (sh.lane_bytes == 32) return launch_range_kpt<KIND, BB, 32>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+    if constexpr (KRB >= 64)
         if (sh.lane_bytes == 64) return launch_range_kpt<KIND, BB, 64>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
-    if constexpr (BB >= 128)
+    if constexpr (KRB >= 128)
         if (sh.lane_bytes == 128) return launch_range_kpt<KIND, BB, 128>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
+    if constexpr (Traits<KIND>::MAP)   // one thread reads keys and values
+        if (sh.lane_bytes == BB) return launch_range_kpt<KIND, BB, BB>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
     return cudaErrorInvalidValue;
 }
 
@@ -212,28 +248,46 @@ cudaError_t launch_range(int op, const View &v, int bucket_bytes, const void *ke
     }
 }
 
-template <int KIND>
-cudaError_t launch_clear(const View &v, unsigned long long phys, unsigned long long capacity, int sm_count,
-                         cudaStream_t s) {
-    const unsigned long long bytes = phys * sizeof(typename Traits<KIND>::Key);   // whole buckets: multiple of 32
+template <int KIND, int BB>
+cudaError_t launch_clear_bb(const View &v, unsigned long long phys, unsigned long long capacity, int sm_count,
+                            cudaStream_t s) {
+    const unsigned long long bytes = v.nb * BB;   // whole buckets: a multiple of 32
     const unsigned long long chunks = bytes / 32;
     unsigned grid = (unsigned)std::min<unsigned long long>((chunks + 255) / 256, (unsigned long long)sm_count * 8);
     if (grid == 0) grid = 1;
-    k_fill_empty<<<grid, 256, 0, s>>>(v.keys, bytes, v.hdr);
+    k_fill_empty<<<grid, 256, 0, s>>>(v.buckets, bytes, v.hdr);
     if (phys > capacity) {
         const unsigned long long pad = phys - capacity;
-        k_pad_tombstones<KIND><<<(unsigned)((pad + 127) / 128), 128, 0, s>>>(v.keys, capacity, pad);
+        k_pad_tombstones<KIND, BB><<<(unsigned)((pad + 127) / 128), 128, 0, s>>>(v, capacity, pad);
     }
     return cudaGetLastError();
 }
 
 template <int KIND>
+cudaError_t launch_clear(const View &v, unsigned long long phys, unsigned long long capacity, int bucket_bytes,
+                         int sm_count, cudaStream_t s) {
+    switch (bucket_bytes) {
+        case 32: return launch_clear_bb<KIND, 32>(v, phys, capacity, sm_count, s);
+        case 64: return launch_clear_bb<KIND, 64>(v, phys, capacity, sm_count, s);
+        case 128: return launch_clear_bb<KIND, 128>(v, phys, capacity, sm_count, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int KIND>
 cudaError_t launch_dump(const View &v, unsigned long long phys, void *keys_out, void *vals_out, unsigned long long cap,
-                        int sm_count, cudaStream_t s) {
+                        int bucket_bytes, int sm_count, cudaStream_t s) {
     using T = Traits<KIND>;
     unsigned grid = (unsigned)std::min<unsigned long long>((phys + 255) / 256, (unsigned long long)sm_count * 8);
     if (grid == 0) grid = 1;
-    k_dump<KIND><<<grid, 256, 0, s>>>(v, phys, (typename T::Key *)keys_out, (typename T::Val *)vals_out, cap);
+    auto ko = (typename T::Key *)keys_out;
+    auto vo = (typename T::Val *)vals_out;
+    switch (bucket_bytes) {
+        case 32: k_dump<KIND, 32><<<grid, 256, 0, s>>>(v, phys, ko, vo, cap); break;
+        case 64: k_dump<KIND, 64><<<grid, 256, 0, s>>>(v, phys, ko, vo, cap); break;
+        case 128: k_dump<KIND, 128><<<grid, 256, 0, s>>>(v, phys, ko, vo, cap); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -261,13 +315,13 @@ cudaError_t launch_rehash(const View &old_v, unsigned long long old_phys, const 
                              cudaStream_t s) {                                                                      \
         return launch_range<KIND>(op, v, bb, keys, vals, n, out, vals_out, sh, skip, s);                            \
     }                                                                                                               \
-    cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int sms,               \
+    cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int bb, int sms,       \
                              cudaStream_t s) {                                                                      \
-        return launch_clear<KIND>(v, phys, cap, sms, s);                                                            \
+        return launch_clear<KIND>(v, phys, cap, bb, sms, s);                                                        \
     }                                                                                                               \
     cudaError_t NAME##_dump(const View &v, unsigned long long phys, void *ko, void *vo, unsigned long long cap,     \
-                            int sms, cudaStream_t s) {                                                              \
-        return launch_dump<KIND>(v, phys, ko, vo, cap, sms, s);                                                     \
+                            int bb, int sms, cudaStream_t s) {                                                      \
+        return launch_dump<KIND>(v, phys, ko, vo, cap, bb, sms, s);                                                 \
     }                                                                                                               \
     cudaError_t NAME##_rehash(const View &ov, unsigned long long ophys, const View &nv, int bb, int sms,            \
                               cudaStream_t s) {                                                                     \

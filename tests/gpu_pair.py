@@ -48,6 +48,20 @@ class Pair:
         self.g = Table(kind, slots, bucket_bytes=bucket_bytes, hash_mode=hash_mode, seed=seed)
         self.o = O.OracleTable(kind, slots)
         if shape:
+            shape = dict(shape)
+            krb = self.g.get_launch(0)["lane_bytes"]          # default lane = whole key region
+            lb = shape.get("lane_bytes", 0)
+            if lb == "full":                                   # maps: keys and values in one read
+                lb = bucket_bytes if kind in O.VAL_DTYPE else krb
+            elif lb == "wide":
+                lb = krb
+            elif lb == "mid":
+                lb = max(krb // 2, 16 if kind in O.VAL_DTYPE else 32)
+            elif lb == "narrow":
+                lb = 16 if kind in O.VAL_DTYPE else 32
+            else:
+                lb = min(int(lb), krb)
+            shape["lane_bytes"] = lb
             for op in (0, 1, 2):
                 self.g.set_launch(op, **shape)
         self.is_map = self.g.is_map

@@ -13,9 +13,12 @@ from oracle import oracle as O
 pytestmark = pytest.mark.gpu
 
 KINDS = (O.SET_U32, O.SET_U64, O.MAP_I64_I32, O.MAP_U64_U64)
-SHAPES = [  # (bucket bytes, lane bytes, keys per group, block, fold)
-    (32, 32, 1, 256, 1), (32, 32, 2, 128, 2), (64, 64, 1, 64, 1), (64, 32, 2, 256, 2), (64, 64, 2, 512, 1),
-    (128, 128, 1, 128, 1), (128, 32, 2, 96, 2), (128, 64, 1, 256, 1), (128, 128, 2, 256, 2),
+SHAPES = [  # (bucket bytes, lane width, keys per group, block, fold); lane widths are
+    # resolved per kind: wide = the whole key region, mid = half, narrow = 16 B (maps) / 32 B (sets),
+    # full = the whole bucket, keys and values (maps; the key region for sets)
+    (32, "wide", 1, 256, 1), (32, "wide", 2, 128, 2), (64, "wide", 1, 64, 1), (64, "narrow", 2, 256, 2),
+    (64, "wide", 2, 512, 1), (128, "wide", 1, 128, 1), (128, "narrow", 2, 96, 2), (128, "mid", 1, 256, 1),
+    (128, "wide", 2, 256, 2), (64, "full", 1, 128, 1), (128, "full", 2, 64, 2),
 ]
 
 
@@ -185,7 +188,8 @@ def test_set_u32_workload_full():
         p.close()
 
 
-@pytest.mark.parametrize("bb,lb,kpt", [(32, 32, 1), (64, 64, 1), (128, 32, 2)])
+@pytest.mark.parametrize("bb,lb,kpt", [(32, "wide", 1), (64, "wide", 1), (64, "full", 1), (128, "narrow", 2),
+                                       (128, "wide", 1)])
 def test_map_u64_load_factor_sweep_scaled(bb, lb, kpt):
     """map<u64,u64> at 2^20 slots: fill to 0.5/0.7/0.8/0.9 in batches, find
     2^16 present and 2^16 absent keys at each step, erase 2^16, contents."""

@@ -1,0 +1,72 @@
+"""Served form: every request's result is the same in the mix (continuous
+batching, merged launches, several lanes overlapping on the GPU, admission
+against a small scratch budget) as when its table's requests are replayed
+alone, one range call at a time, in arrival order.  Exact integer results;
+duplicate keys inside one request compared as a multiset (compare.py)."""
+import numpy as np
+import pytest
+import torch
+
+import compare as C
+from paper_1908_05936_gb300 import _lib as L
+from paper_1908_05936_gb300.serve import Server, ServedRequest
+from paper_1908_05936_gb300.table import Table, to_numpy
+from workloads import recipes, splitmix
+
+pytestmark = pytest.mark.gpu
+
+
+def make_tables(n_tables, slots, prefill, seed):
+    tabs = []
+    for t in range(n_tables):
+        tab = Table(L.MAP_U64_U64, slots, bucket_bytes=128)
+        k = splitmix.stream_u64(7000 + t, seed, 0, prefill)
+        tab.insert(torch.from_numpy(k.view(np.int64)).cuda(),
+                   torch.from_numpy(splitmix.value_of(k).view(np.int64)).cuda(), status=False)
+        tabs.append(tab)
+    torch.cuda.synchronize()
+    return tabs
+
+
+def make_requests(n_req, n_tables, rate, seed, max_log2=14):
+    cdf = recipes.zipf_cdf(1 << 16)
+    out = []
+    for q in recipes.served_requests(n_req, n_tables, rate, seed=seed, max_log2=max_log2):
+        keys = recipes.zipf_keys(q.table, q.key_stream, q.n, cdf, seed)
+        kt = torch.from_numpy(keys.view(np.int64)).pin_memory()
+        vt = torch.from_numpy(splitmix.value_of(keys).view(np.int64)).pin_memory() if q.op == 0 else None
+        out.append(ServedRequest(q.rid, q.table, q.op, kt, vt, q.arrival))
+    return out
+
+
+@pytest.mark.parametrize("merge", [True, False])
+def test_served_equals_alone(merge):
+    from paper_1908_05936_gb300 import build
+    build.build()
+    n_tables, slots = 6, 1 << 18
+    mix_tabs = make_tables(n_tables, slots, 1 << 16, seed=1)
+    alone_tabs = make_tables(n_tables, slots, 1 << 16, seed=1)
+    reqs = make_requests(240, n_tables, rate=20000.0, seed=3)
+    srv = Server(mix_tabs, slot_bytes=1 << 20, lanes=3, merge=merge, depth=2, max_items=8)
+    stats = srv.run(reqs, realtime=True)
+    assert stats["requests"] == len(reqs)
+    assert stats["launches"] == len(reqs) if not merge else stats["launches"] <= len(reqs)
+    for r in sorted(reqs, key=lambda r: r.rid):
+        t = alone_tabs[r.table]
+        k = r.keys.cuda()
+        if r.op == L.OP_INSERT:
+            st = to_numpy(t.insert(k, r.vals.cuda()), np.uint8)
+            C.assert_status(r.keys.numpy(), r.status, st, f"request {r.rid} insert")
+        elif r.op == L.OP_FIND:
+            f, v = t.find(k)
+            C.assert_find(r.status, r.values, to_numpy(f, np.uint8), to_numpy(v, np.int64),
+                          f"request {r.rid} find")
+        else:
+            st = to_numpy(t.erase(k), np.uint8)
+            C.assert_status(r.keys.numpy(), r.status, st, f"request {r.rid} erase")
+    for a, b in zip(mix_tabs, alone_tabs):
+        ka, va = a.dump_numpy()
+        kb, vb = b.dump_numpy()
+        C.assert_contents(ka, va, kb, vb)
+    for t in mix_tabs + alone_tabs:
+        t.close()
