@@ -140,6 +140,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------ replicas --
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The slowest rank's time: every rank runs its own independent table (the
+    units are independent, so there is no data-path collective); the job's
+    time is the max over ranks, taken with one all-reduce of a scalar."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job Mops/s: the units all ranks processed over the slowest time."""
+    return units_per_rank * world / (max_ms * 1e-3) / 1e6
+
+
 # --------------------------------------------------------------- gpu arm --
 
 def run_gpu(args, rank: int, world: int):
@@ -221,10 +241,7 @@ def run_gpu(args, rank: int, world: int):
         torch.distributed.barrier()
     clk = clocks.stop()
     elapsed_ms = start.elapsed_time(end)
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
 
     per = {}
     for name, n, a, b in calls:
@@ -245,8 +262,7 @@ def run_gpu(args, rank: int, world: int):
                                           (sum(x[1] for x in per["insert"][i::nb]) * 1e-3) / 1e6, 1)}
         for i in range(nb)]
 
-    ops = wl.ops_per_step() * args.steps * world
-    value = ops / (elapsed_ms * 1e-3) / 1e6
+    value = job_throughput(wl.ops_per_step() * args.steps, world, elapsed_ms)
 
     # roofline of the dominant kernel (largest share of the timed region)
     kinds = {"insert": "insert", "find_hit": "find", "find_miss": "find", "erase": "erase"}
@@ -274,10 +290,37 @@ def run_gpu(args, rank: int, world: int):
         "gpu_launches": len(calls) * world,
         "check": {"size_after_step": size_after, "expected": expected_size},
     }
+    out["other_ops"] = time_rehash_dump(t, torch)
     if not args.no_e2e:
         out["e2e"] = run_e2e(t, wl, fill, vals, hit, miss, er, stream)
     t.close()
     return out
+
+
+def time_rehash_dump(t, torch):
+    """Host-called whole-table operations on the table a step left behind
+    (load factor 0.55 plus the step's tombstones), timed once each by wall
+    clock (both synchronise): rehash to the same capacity, which purges the
+    tombstones, then dump of every stored pair, and size."""
+    torch.cuda.synchronize()
+    st0 = t.stats()
+    t0 = time.perf_counter()
+    t.rehash(st0["capacity"])
+    rehash_s = time.perf_counter() - t0
+    st1 = t.stats()
+    t0 = time.perf_counter()
+    k, v = t.dump()
+    torch.cuda.synchronize()
+    dump_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    live = t.size()
+    size_s = time.perf_counter() - t0
+    assert len(k) == live == st1["live"] == st0["live"]
+    del k, v
+    return {"rehash": {"ms": round(rehash_s * 1e3, 2), "live": st0["live"], "used_before": st0["used"],
+                       "used_after": st1["used"], "mkeys_per_s": round(st0["live"] / rehash_s / 1e6, 1)},
+            "dump": {"ms": round(dump_s * 1e3, 2), "mkeys_per_s": round(live / dump_s / 1e6, 1)},
+            "size": {"us": round(size_s * 1e6, 1)}}
 
 
 def run_e2e(t, wl, fill, vals, hit, miss, er, stream):

@@ -14,8 +14,17 @@ namespace hc {
 // (A persistent grid-stride form that prefetched the next tile measured
 // 1.3-2x slower on GB300 for every shape.)
 
+// Launch bounds (threads per block[, minimum resident blocks]): a build option,
+// since capping registers trades spills for resident warps.
+#ifndef HC_INSERT_BOUNDS
+#define HC_INSERT_BOUNDS 512
+#endif
+#ifndef HC_FIND_BOUNDS
+#define HC_FIND_BOUNDS 512
+#endif
+
 template <int KIND, int BB, int LB, int KPT>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(HC_INSERT_BOUNDS)
 k_insert(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
          uint8_t *status, int fold, const uint8_t *skip) {
     constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
@@ -28,7 +37,7 @@ k_insert(View v, const typename Traits<KIND>::Key *keys, const typename Traits<K
 }
 
 template <int KIND, int BB, int LB, int KPT>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(HC_FIND_BOUNDS)
 k_find(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *found,
        typename Traits<KIND>::Val *vals_out) {
     constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
@@ -40,7 +49,7 @@ k_find(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *fou
 }
 
 template <int KIND, int BB, int LB, int KPT>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(HC_FIND_BOUNDS)
 k_erase(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status, int fold) {
     constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

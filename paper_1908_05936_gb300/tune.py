@@ -1,0 +1,178 @@
+"""Autotuner of launch shapes (lane width = lanes per key, keys in flight,
+block size) per container kind, operation and bucket size, on the current
+GPU.  Results never depend on the shape; only speed does.
+
+    python -m paper_1908_05936_gb300.tune [--kinds map_u64_u64,set_u64] [--slots-log2 26]
+
+For each (kind, bucket bytes) it fills a table to load factor 0.8 in batches
+of 2^(slots_log2 - 2) keys, then times every candidate shape on insert (the
+last batch of the fill), find (all present), find (all absent) and erase
+with CUDA events, and keeps the fastest shape per operation.  The winners are
+written to a JSON cache keyed by device name and SM count
+(`tuned.json` next to this file); `apply()` installs them on a table.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+
+import torch
+
+from . import _lib as L
+from .table import KIND_NAMES, Table
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+LANES = (16, 32, 64, 128)
+KEYS_IN_FLIGHT = (1, 2)
+BLOCKS = (64, 128, 256)
+
+
+def device_key() -> str:
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}/{p.multi_processor_count}SM"
+
+
+def _keys(kind: int, stream: int, start: int, n: int):
+    from workloads import gpu as G
+    if kind == L.SET_U32:
+        return G.stream_u32(stream, 0, start, n)
+    return G.stream_u64(stream, 0, start, n)
+
+
+def _vals(kind: int, keys):
+    from workloads import gpu as G
+    if kind == L.MAP_U64_U64:
+        return G.value_of(keys)
+    if kind == L.MAP_I64_I32:
+        return (G.value_of(keys) & 0x7FFFFFFF).to(torch.int32)
+    return None
+
+
+def _time(fn, reps: int = 3) -> float:
+    s = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _time_once(fn) -> float:
+    s = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def candidates(table: Table) -> list[dict]:
+    default = table.get_launch(0)["lane_bytes"]          # the bucket's key region
+    lanes = [lb for lb in LANES if lb <= default and (lb >= 32 or table.is_map)]
+    if table.is_map:
+        lanes.append(table.bucket_bytes)                  # keys and values in one read
+    return [dict(lane_bytes=lb, keys_per_group=k, block=b) for lb in lanes for k in KEYS_IN_FLIGHT for b in BLOCKS]
+
+
+def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0.8) -> dict:
+    slots = 1 << slots_log2
+    n_fill = int(lf * slots)
+    batch = 1 << (slots_log2 - 2)
+    t = Table(kind, slots, bucket_bytes=bucket_bytes)
+    fill = _keys(kind, 3, 0, n_fill)
+    vals = _vals(kind, fill)
+    for off in range(0, n_fill - batch, batch):
+        t.insert(fill[off:off + batch], vals[off:off + batch] if vals is not None else None, status=False)
+    last = fill[n_fill - batch:]
+    last_v = vals[n_fill - batch:] if vals is not None else None
+    hit = fill[:batch]
+    miss = _keys(kind, 4, 0, batch)
+    out = torch.empty(batch, dtype=torch.uint8, device="cuda")
+    vout = torch.empty(batch, dtype=torch.int32 if kind == L.MAP_I64_I32 else torch.int64, device="cuda") \
+        if t.is_map else False
+    results = {"insert": [], "find_hit": [], "find_miss": [], "erase": []}
+    t.insert(last, last_v, status=False)                  # the table starts at the target load factor
+    for c in candidates(t):
+        for op in (0, 1, 2):
+            t.set_launch(op, fold=2, **c)
+
+        def ins():
+            t.insert(last, last_v, status=out)
+
+        def era():
+            t.erase(last, status=out)
+
+        # erase / re-insert the last batch: each insert stores new keys into a
+        # table at the target load factor, each erase removes present keys
+        e_ms, i_ms = [], []
+        for _ in range(2):
+            e_ms.append(_time_once(era))
+            i_ms.append(_time_once(ins))
+        results["insert"].append((min(i_ms), c))
+        results["erase"].append((min(e_ms), c))
+        results["find_hit"].append((_time(lambda: t.find(hit, found=out, vals_out=vout)), c))
+        results["find_miss"].append((_time(lambda: t.find(miss, found=out, vals_out=vout)), c))
+    t.close()
+    best = {}
+    for op, lst in results.items():
+        ms, c = min(lst, key=lambda x: x[0])
+        best[op] = dict(c, ms=round(ms, 4), mops=round(batch / ms / 1e3, 1))
+    return best
+
+
+def tune(kinds: list[int], buckets=(32, 64, 128), slots_log2: int = 26) -> dict:
+    res = {}
+    for kind in kinds:
+        name = [k for k, v in KIND_NAMES.items() if v == kind][0]
+        for bb in buckets:
+            res[f"{name}/{bb}"] = tune_table(kind, bb, slots_log2)
+    cache = {}
+    if os.path.exists(CACHE):
+        with open(CACHE) as f:
+            cache = json.load(f)
+    cache.setdefault(device_key(), {}).update(res)
+    with open(CACHE, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    return res
+
+
+def apply(table: Table) -> bool:
+    """Install the tuned shapes for this table's kind and bucket size on the
+    current GPU, if the cache has them."""
+    if not os.path.exists(CACHE):
+        return False
+    with open(CACHE) as f:
+        cache = json.load(f).get(device_key(), {})
+    name = [k for k, v in KIND_NAMES.items() if v == table.kind][0]
+    best = cache.get(f"{name}/{table.bucket_bytes}")
+    if not best:
+        return False
+    for op, key in ((L.OP_INSERT, "insert"), (L.OP_FIND, "find_hit"), (L.OP_ERASE, "erase")):
+        b = best[key]
+        table.set_launch(op, lane_bytes=b["lane_bytes"], keys_per_group=b["keys_per_group"], block=b["block"])
+    return True
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kinds", default="map_u64_u64,set_u64,set_u32,map_i64_i32")
+    ap.add_argument("--buckets", default="32,64,128")
+    ap.add_argument("--slots-log2", type=int, default=26)
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    kinds = [KIND_NAMES[k] for k in a.kinds.split(",")]
+    print(json.dumps(tune(kinds, tuple(int(b) for b in a.buckets.split(",")), a.slots_log2)))
+
+
+if __name__ == "__main__":
+    main()

