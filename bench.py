@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-sample-log2", type=int, default=22)
+    ap.add_argument("--cpu-sample-log2", type=int, default=24)
     ap.add_argument("--workload", default="map_sweep", choices=["map_sweep", "multi_table", "served", "rgbd"])
     ap.add_argument("--rgbd-slots", type=int, default=12_500_000)
     ap.add_argument("--rgbd-hash", type=int, default=1, help="1 = the paper's spatial hash, 0 = mix64")

@@ -16,15 +16,21 @@ namespace hc {
 
 // Launch bounds (threads per block[, minimum resident blocks]): a build option,
 // since capping registers trades spills for resident warps.
-#ifndef HC_INSERT_BOUNDS
-#define HC_INSERT_BOUNDS 512
+#ifndef HC_INSERT_MAXT
+#define HC_INSERT_MAXT 512
 #endif
-#ifndef HC_FIND_BOUNDS
-#define HC_FIND_BOUNDS 512
+#ifndef HC_INSERT_MINB
+#define HC_INSERT_MINB 1
+#endif
+#ifndef HC_FIND_MAXT
+#define HC_FIND_MAXT 512
+#endif
+#ifndef HC_FIND_MINB
+#define HC_FIND_MINB 1
 #endif
 
 template <int KIND, int BB, int LB, int KPT>
-__global__ void __launch_bounds__(HC_INSERT_BOUNDS)
+__global__ void __launch_bounds__(HC_INSERT_MAXT, HC_INSERT_MINB)
 k_insert(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
          uint8_t *status, int fold, const uint8_t *skip) {
     constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
@@ -37,7 +43,7 @@ k_insert(View v, const typename Traits<KIND>::Key *keys, const typename Traits<K
 }
 
 template <int KIND, int BB, int LB, int KPT>
-__global__ void __launch_bounds__(HC_FIND_BOUNDS)
+__global__ void __launch_bounds__(HC_FIND_MAXT, HC_FIND_MINB)
 k_find(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *found,
        typename Traits<KIND>::Val *vals_out) {
     constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
@@ -49,7 +55,7 @@ k_find(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *fou
 }
 
 template <int KIND, int BB, int LB, int KPT>
-__global__ void __launch_bounds__(HC_FIND_BOUNDS)
+__global__ void __launch_bounds__(HC_FIND_MAXT, HC_FIND_MINB)
 k_erase(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status, int fold) {
     constexpr int TILE = Shape<KIND, BB, LB, KPT>::TILE;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
