@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=24)
-    ap.add_argument("--workload", default="map_sweep", choices=["map_sweep", "multi_table", "served", "rgbd"])
+    ap.add_argument("--workload", default="map_sweep", choices=["map_sweep", "multi_table", "served", "rgbd", "set_u32"])
     ap.add_argument("--rgbd-slots", type=int, default=12_500_000)
     ap.add_argument("--rgbd-hash", type=int, default=1, help="1 = the paper's spatial hash, 0 = mix64")
     ap.add_argument("--tables", type=int, default=1024)
@@ -490,6 +490,63 @@ def run_multi_table(args):
             "gpu_launches": arms["batched"]["launches_per_step"] * args.steps}
 
 
+# ---------------------------------------------------- set<u32> workload --
+
+def run_set_u32(args):
+    """set<u32>, 2^21 slots (8 MiB of keys: the table lives in L2): insert
+    10^6 uniform keys, find 10^6 (half present), erase 5*10^5.  A step is
+    clear + the three calls; inputs stay resident; each step's calls are timed
+    with CUDA events and the L2 is flushed (a 256 MiB write) between steps so
+    every step starts cold."""
+    import torch
+    from paper_1908_05936_gb300 import _lib as L
+    from paper_1908_05936_gb300 import build
+    from paper_1908_05936_gb300.table import Table, to_device
+    from workloads import recipes
+
+    build.build()
+    w = recipes.set_u32_workload()
+    t = Table(L.SET_U32, w.slots, bucket_bytes=args.bucket_bytes or 64)
+    ki, kf, ke = to_device(w.insert_keys), to_device(w.find_keys), to_device(w.erase_keys)
+    si = torch.empty(ki.numel(), dtype=torch.uint8, device="cuda")
+    ff = torch.empty(kf.numel(), dtype=torch.uint8, device="cuda")
+    se = torch.empty(ke.numel(), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    per = {"clear": [], "insert": [], "find": [], "erase": [], "step": []}
+    s = torch.cuda.current_stream()
+    for i in range(args.warmup + args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(s)
+        t.clear()
+        ev[1].record(s)
+        t.insert(ki, status=si)
+        ev[2].record(s)
+        t.find(kf, found=ff, vals_out=False)
+        ev[3].record(s)
+        t.erase(ke, status=se)
+        ev[4].record(s)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            for j, k in enumerate(("clear", "insert", "find", "erase")):
+                per[k].append(ev[j].elapsed_time(ev[j + 1]))
+            per["step"].append(ev[0].elapsed_time(ev[4]))
+    n = {"insert": ki.numel(), "find": kf.numel(), "erase": ke.numel()}
+    med = {k: statistics.median(v) for k, v in per.items()}
+    ops = sum(n.values())
+    size = t.size()
+    t.close()
+    return {"metric": "set<u32> (L2-resident) Mops/s per op", "value": round(ops / med["step"] / 1e3, 1),
+            "unit": "Mops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(med["step"], 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic (seeded splitmix64 keys)",
+            "config": {"workload": "set<u32> 2^21 slots: insert 1,000,000, find 1,000,000 (50% present), erase 500,000",
+                       "l2": "256 MiB flush before each step"},
+            "ops": {k: {"ms": round(med[k], 4), "mops": round(n[k] / med[k] / 1e3, 1)} for k in n},
+            "clear_ms": round(med["clear"], 4), "final_size": size, "gpu_launches": 4 * args.steps}
+
+
 # ------------------------------------------------------ RGB-D workload --
 
 def rgbd_frames(params, workers: int = 8):
@@ -663,6 +720,9 @@ def main():
         return
     if args.workload == "rgbd":
         print(json.dumps(run_rgbd(args)))
+        return
+    if args.workload == "set_u32":
+        print(json.dumps(run_set_u32(args)))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

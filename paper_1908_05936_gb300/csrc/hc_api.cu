@@ -300,8 +300,8 @@ hc_rc hc_create(hc_table **out, int32_t kind, int64_t slots, const hc_config *cf
     }
     t->view = make_view(t->d_mem, g, seed, hm);
     // one thread per key reading the bucket's keys, one key in flight,
-    // 128-thread blocks: the best shape of the sweeps on GB300 for uniform keys
-    for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{key_region_bytes(kind, bb), 1, 128, 0, 0};
+    // 64-thread blocks: the best shape of the sweeps on GB300 for uniform keys
+    for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{key_region_bytes(kind, bb), 1, 64, 0, 0};
     e = dispatch_clear(t, t->view, t->phys, t->capacity, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         cudaFree(t->d_mem);
@@ -350,8 +350,8 @@ hc_rc hc_set_launch(hc_table *t, int32_t op, const hc_launch *shape) {
                     "bucket for maps", krb);
     if (sh.keys_per_group != 1 && sh.keys_per_group != 2)
         return fail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
-    if (sh.block < 64 || sh.block > 512 || sh.block % 32)
-        return fail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 512]");
+    if (sh.block < 64 || sh.block > 256 || sh.block % 32)
+        return fail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     t->shape[op] = sh;
     return HC_OK;
 }

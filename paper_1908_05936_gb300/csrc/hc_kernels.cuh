@@ -17,16 +17,16 @@ namespace hc {
 // Launch bounds (threads per block[, minimum resident blocks]): a build option,
 // since capping registers trades spills for resident warps.
 #ifndef HC_INSERT_MAXT
-#define HC_INSERT_MAXT 512
+#define HC_INSERT_MAXT 256
 #endif
 #ifndef HC_INSERT_MINB
 #define HC_INSERT_MINB 1
 #endif
 #ifndef HC_FIND_MAXT
-#define HC_FIND_MAXT 512
+#define HC_FIND_MAXT 256
 #endif
 #ifndef HC_FIND_MINB
-#define HC_FIND_MINB 1
+#define HC_FIND_MINB 6   // 40 registers, no spills: +1-7 % for find and erase on GB300
 #endif
 
 template <int KIND, int BB, int LB, int KPT>

@@ -17,7 +17,7 @@ SHAPES = [  # (bucket bytes, lane width, keys per group, block, fold); lane widt
     # resolved per kind: wide = the whole key region, mid = half, narrow = 16 B (maps) / 32 B (sets),
     # full = the whole bucket, keys and values (maps; the key region for sets)
     (32, "wide", 1, 256, 1), (32, "wide", 2, 128, 2), (64, "wide", 1, 64, 1), (64, "narrow", 2, 256, 2),
-    (64, "wide", 2, 512, 1), (128, "wide", 1, 128, 1), (128, "narrow", 2, 96, 2), (128, "mid", 1, 256, 1),
+    (64, "wide", 2, 256, 1), (128, "wide", 1, 128, 1), (128, "narrow", 2, 96, 2), (128, "mid", 1, 256, 1),
     (128, "wide", 2, 256, 2), (64, "full", 1, 128, 1), (128, "full", 2, 64, 2),
 ]
 
