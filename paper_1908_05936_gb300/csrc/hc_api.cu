@@ -108,6 +108,8 @@ hc::View make_view(void *mem, const Geometry &g, unsigned long long seed, int ha
     v.seed = seed;
     v.hash_mode = hash_mode;
     v.pad_from = g.pad_from;
+    v.rotate = 0;
+    v.reserved = 0;
     return v;
 }
 
@@ -185,7 +187,9 @@ hc_rc run_range(hc_table *t, int op, const void *keys, const void *vals, long lo
     if (rc != HC_OK || n == 0) return rc;
     hc::LaunchShape sh = t->shape[op];
     sh.sms = sm_count_of(t->device);
-    cudaError_t e = dispatch_range(t->kind, op, t->view, t->bucket_bytes, keys, is_map(t->kind) ? vals : nullptr, n,
+    hc::View v = t->view;
+    v.rotate = n > (long long)v.nb ? 1 : 0;        // several inserters per bucket: spread them
+    cudaError_t e = dispatch_range(t->kind, op, v, t->bucket_bytes, keys, is_map(t->kind) ? vals : nullptr, n,
                                    out, is_map(t->kind) ? vals_out : nullptr, sh, skip, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the range kernel");
     return HC_OK;
@@ -302,6 +306,8 @@ hc_rc hc_create(hc_table **out, int32_t kind, int64_t slots, const hc_config *cf
     // one thread per key reading the bucket's keys, one key in flight,
     // 64-thread blocks: the best shape of the sweeps on GB300 for uniform keys
     for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{key_region_bytes(kind, bb), 1, 64, 0, 0};
+    // maps look up with the streaming kernel: 4 keys per thread, 2 in flight
+    if (is_map(kind)) t->shape[hc::OP_FIND].keys_per_group = 4;
     e = dispatch_clear(t, t->view, t->phys, t->capacity, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         cudaFree(t->d_mem);
@@ -348,8 +354,9 @@ hc_rc hc_set_launch(hc_table *t, int32_t op, const hc_launch *shape) {
         return fail(HC_ERR_ARG,
                     "lane_bytes must be 32, 64 or 128 (16 for maps) and at most the %d-byte key region, or the whole "
                     "bucket for maps", krb);
-    if (sh.keys_per_group != 1 && sh.keys_per_group != 2)
-        return fail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
+    if (sh.keys_per_group != 1 && sh.keys_per_group != 2 &&
+        !((sh.keys_per_group == 4 || sh.keys_per_group == 8) && op == hc::OP_FIND && sh.lane_bytes == krb))
+        return fail(HC_ERR_ARG, "keys_per_group must be 1 or 2 (4 or 8: streaming find, lane = key region)");
     if (sh.block < 64 || sh.block > 256 || sh.block % 32)
         return fail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     t->shape[op] = sh;

@@ -38,6 +38,7 @@ struct BatchItemDev {
 struct PhaseDesc {
     int kind;
     int op;
+    int bb;        // bucket bytes of every table in the phase
     int item0;
     int n_items;
     long long n_chunks;
@@ -56,12 +57,16 @@ __device__ __forceinline__ void run_chunk(const BatchItemDev &it, long long k0, 
     if constexpr (OP != OP_FIND) flush_counts(it.v, cnt);
 }
 
-// WIDE: one thread per key reading the item's whole bucket (maps: keys and
-// values) or key region (sets); otherwise 32-byte lanes.
-template <int KIND, int OP, int WIDE, int KPT>
+// One phase launch covers items of one kind, one op and one bucket size (so
+// each launch is a small specialisation).  WIDE: one thread per key reading
+// the whole bucket (maps: keys and values) or key region (sets); otherwise
+// 32-byte lanes.
+template <int KIND, int OP, int BB, int WIDE, int KPT>
 __global__ void __launch_bounds__(256)
 k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_chunks, int tile,
               unsigned long long *counter) {
+    constexpr int KRB = Slots<KIND, BB>::KRB;
+    constexpr int LB = WIDE ? (Traits<KIND>::MAP ? BB : KRB) : (KRB < 32 ? KRB : 32);
     const int lane = threadIdx.x & 31;
     while (true) {
         unsigned long long c = 0;
@@ -78,14 +83,7 @@ k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_c
         const BatchItemDev it = items[lo];
         const long long k0 = ((long long)c - it.chunk_begin) * tile;
         const long long k1 = k0 + tile < it.n ? k0 + tile : it.n;
-        // wide: maps read the whole bucket (keys and values), sets the key region
-        constexpr bool M = Traits<KIND>::MAP;
-        constexpr int K32 = Slots<KIND, 32>::KRB, K64 = Slots<KIND, 64>::KRB, K128 = Slots<KIND, 128>::KRB;
-        switch (it.bb) {
-            case 32: run_chunk<KIND, OP, 32, WIDE ? (M ? 32 : K32) : (K32 < 32 ? K32 : 32), KPT>(it, k0, k1); break;
-            case 64: run_chunk<KIND, OP, 64, WIDE ? (M ? 64 : K64) : 32, KPT>(it, k0, k1); break;
-            default: run_chunk<KIND, OP, 128, WIDE ? (M ? 128 : K128) : 32, KPT>(it, k0, k1); break;
-        }
+        run_chunk<KIND, OP, BB, LB, KPT>(it, k0, k1);
     }
 }
 
@@ -95,25 +93,32 @@ __global__ void k_zero_counters(unsigned long long *c, int n) {
 
 using PhaseKernel = void (*)(const BatchItemDev *, int, long long, int, unsigned long long *);
 
-template <int KIND, int OP>
+template <int KIND, int OP, int BB>
 PhaseKernel pick_lb_kpt(int lb, int kpt) {
-    if (lb == 0) return kpt == 1 ? k_batch_phase<KIND, OP, 1, 1> : k_batch_phase<KIND, OP, 1, 2>;
-    return kpt == 1 ? k_batch_phase<KIND, OP, 0, 1> : k_batch_phase<KIND, OP, 0, 2>;
+    if (lb == 0) return kpt == 1 ? k_batch_phase<KIND, OP, BB, 1, 1> : k_batch_phase<KIND, OP, BB, 1, 2>;
+    return kpt == 1 ? k_batch_phase<KIND, OP, BB, 0, 1> : k_batch_phase<KIND, OP, BB, 0, 2>;
+}
+
+template <int KIND, int OP>
+PhaseKernel pick_bb(int bb, int lb, int kpt) {
+    if (bb == 32) return pick_lb_kpt<KIND, OP, 32>(lb, kpt);
+    if (bb == 64) return pick_lb_kpt<KIND, OP, 64>(lb, kpt);
+    return pick_lb_kpt<KIND, OP, 128>(lb, kpt);
 }
 
 template <int KIND>
-PhaseKernel pick_op(int op, int lb, int kpt) {
-    if (op == OP_INSERT) return pick_lb_kpt<KIND, OP_INSERT>(lb, kpt);
-    if (op == OP_FIND) return pick_lb_kpt<KIND, OP_FIND>(lb, kpt);
-    return pick_lb_kpt<KIND, OP_ERASE>(lb, kpt);
+PhaseKernel pick_op(int op, int bb, int lb, int kpt) {
+    if (op == OP_INSERT) return pick_bb<KIND, OP_INSERT>(bb, lb, kpt);
+    if (op == OP_FIND) return pick_bb<KIND, OP_FIND>(bb, lb, kpt);
+    return pick_bb<KIND, OP_ERASE>(bb, lb, kpt);
 }
 
-PhaseKernel pick_kernel(int kind, int op, int lb, int kpt) {
+PhaseKernel pick_kernel(int kind, int op, int bb, int lb, int kpt) {
     switch (kind) {
-        case KIND_SET_U32: return pick_op<KIND_SET_U32>(op, lb, kpt);
-        case KIND_SET_U64: return pick_op<KIND_SET_U64>(op, lb, kpt);
-        case KIND_MAP_I64_I32: return pick_op<KIND_MAP_I64_I32>(op, lb, kpt);
-        default: return pick_op<KIND_MAP_U64_U64>(op, lb, kpt);
+        case KIND_SET_U32: return pick_op<KIND_SET_U32>(op, bb, lb, kpt);
+        case KIND_SET_U64: return pick_op<KIND_SET_U64>(op, bb, lb, kpt);
+        case KIND_MAP_I64_I32: return pick_op<KIND_MAP_I64_I32>(op, bb, lb, kpt);
+        default: return pick_op<KIND_MAP_U64_U64>(op, bb, lb, kpt);
     }
 }
 
@@ -150,12 +155,12 @@ hc_rc bcuda(cudaError_t e, const char *what) {
 hc_rc enqueue(hc_batch *b, cudaStream_t s) {
     const int n_ctr = (int)b->phases.size();
     if (n_ctr == 0) return HC_OK;
-    hc::k_zero_counters<<<1, 32, 0, s>>>(b->d_counters, n_ctr);
+    hc::k_zero_counters<<<1, 64, 0, s>>>(b->d_counters, n_ctr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda(e, "resetting the batch counters");
     for (size_t p = 0; p < b->phases.size(); ++p) {
         const hc::PhaseDesc &ph = b->phases[p];
-        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, b->lane_bytes, b->kpt);
+        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, b->lane_bytes, b->kpt);
         k<<<b->grid[p], b->block, 0, s>>>(b->d_items + ph.item0, ph.n_items, ph.n_chunks, b->tile,
                                           b->d_counters + ph.counter);
         e = cudaGetLastError();
@@ -188,14 +193,15 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
     std::vector<hc::BatchItemDev> dev;
     std::vector<hc::PhaseDesc> phases;
     for (int op = 0; op < 3; ++op) {
-        for (int kind = 0; kind < 4; ++kind) {
-            hc::PhaseDesc ph{kind, op, (int)dev.size(), 0, 0, (int)phases.size()};
+        for (int kind = 0; kind < 4; ++kind)
+        for (int bb = 32; bb <= 128; bb *= 2) {
+            hc::PhaseDesc ph{kind, op, bb, (int)dev.size(), 0, 0, (int)phases.size()};
             for (int64_t i = 0; i < n_items; ++i) {
                 const hc_batch_item &it = items[i];
                 if (!it.table || it.table->magic != HC_TABLE_MAGIC) return bfail(HC_ERR_ARG, "item with a bad table");
                 if (it.op < 0 || it.op > 2) return bfail(HC_ERR_ARG, "item with a bad op");
                 if (it.n < 0) return bfail(HC_ERR_ARG, "item with n < 0");
-                if (it.op != op || it.table->kind != kind || it.n == 0) continue;
+                if (it.op != op || it.table->kind != kind || it.table->bucket_bytes != bb || it.n == 0) continue;
                 const bool map = kind >= HC_MAP_I64_I32;
                 const int kb = kind == HC_SET_U32 ? 4 : 8;
                 if (!it.d_keys || reinterpret_cast<uintptr_t>(it.d_keys) % kb)
@@ -204,6 +210,7 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
                 if (op == HC_OP_FIND && !it.d_out) return bfail(HC_ERR_ARG, "find item without a found array");
                 hc::BatchItemDev d{};
                 d.v = it.table->view;
+                d.v.rotate = it.n > (long long)d.v.nb ? 1 : 0;
                 d.keys = it.d_keys;
                 d.vals = map ? it.d_vals : nullptr;
                 d.out = it.d_out;
@@ -230,7 +237,7 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
     b->phases = phases;
     cudaError_t e = cudaGetDevice(&b->device);
     const size_t items_bytes = (dev.size() * sizeof(hc::BatchItemDev) + 255) / 256 * 256;
-    const size_t bytes = items_bytes + 256;
+    const size_t bytes = items_bytes + 512;   // up to 36 phase counters
     if (e == cudaSuccess) e = cudaMalloc(&b->d_mem, bytes);
     if (e != cudaSuccess) {
         delete b;
@@ -248,7 +255,7 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
         int per_sm = c.blocks_per_sm;
         if (per_sm <= 0) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, hc::pick_kernel(phases[p].kind, phases[p].op, lb, kpt), block, 0);
+                &per_sm, hc::pick_kernel(phases[p].kind, phases[p].op, phases[p].bb, lb, kpt), block, 0);
             if (per_sm <= 0) per_sm = 1;
         }
         long long g = (long long)sms * per_sm;
@@ -317,11 +324,11 @@ HC_API hc_rc hc_batch_destroy(hc_batch *b) {
 namespace {
 
 constexpr int kNoAllocMaxItems = 1024;   // items per call (104 KiB of descriptors)
-constexpr int kNoAllocMaxPhases = 12;    // 3 operations x 4 container kinds
+constexpr int kNoAllocMaxPhases = 36;    // 3 operations x 4 container kinds x 3 bucket sizes
 
 struct NoAllocScratch {
     hc::BatchItemDev items[kNoAllocMaxItems];
-    unsigned long long counters[16];
+    unsigned long long counters[64];
 };
 
 }  // namespace
@@ -380,14 +387,15 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
     hc::PhaseDesc phases[kNoAllocMaxPhases];
     int n_phases = 0, n_dev = 0;
     for (int op = 0; op < 3; ++op) {
-        for (int kind = 0; kind < 4; ++kind) {
-            hc::PhaseDesc ph{kind, op, n_dev, 0, 0, n_phases};
+        for (int kind = 0; kind < 4; ++kind)
+        for (int bb = 32; bb <= 128; bb *= 2) {
+            hc::PhaseDesc ph{kind, op, bb, n_dev, 0, 0, n_phases};
             for (int64_t i = 0; i < n_items; ++i) {
                 const hc_batch_item &it = items[i];
                 if (!it.table || it.table->magic != HC_TABLE_MAGIC) return bfail(HC_ERR_ARG, "item with a bad table");
                 if (it.op < 0 || it.op > 2) return bfail(HC_ERR_ARG, "item with a bad op");
                 if (it.n < 0) return bfail(HC_ERR_ARG, "item with n < 0");
-                if (it.op != op || it.table->kind != kind || it.n == 0) continue;
+                if (it.op != op || it.table->kind != kind || it.table->bucket_bytes != bb || it.n == 0) continue;
                 const bool map = kind >= HC_MAP_I64_I32;
                 const int kb = kind == HC_SET_U32 ? 4 : 8;
                 if (!it.d_keys || reinterpret_cast<uintptr_t>(it.d_keys) % kb)
@@ -397,6 +405,7 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
                 hc::BatchItemDev &d = t_noalloc_items[n_dev++];
                 d = hc::BatchItemDev{};
                 d.v = it.table->view;
+                d.v.rotate = it.n > (long long)d.v.nb ? 1 : 0;
                 d.keys = it.d_keys;
                 d.vals = map ? it.d_vals : nullptr;
                 d.out = it.d_out;
@@ -430,12 +439,12 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
                         cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return bcuda(e, "copying the batch descriptors");
     // the chunk counters keep the previous call's values: reset them first
-    hc::k_zero_counters<<<1, 32, 0, s>>>(scratch->counters, n_phases);
+    hc::k_zero_counters<<<1, 64, 0, s>>>(scratch->counters, n_phases);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda(e, "resetting the chunk counters");
     for (int p = 0; p < n_phases; ++p) {
         const hc::PhaseDesc &ph = phases[p];
-        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, lb, kpt);
+        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, lb, kpt);
         int per_sm = c.blocks_per_sm;
         if (per_sm <= 0) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0);
@@ -472,7 +481,7 @@ extern "C" {
 
 HC_API int64_t hc_batch_scratch_bytes(int64_t n_items) {
     if (n_items < 0 || n_items > kRunMaxItems) return -1;
-    return (int64_t)((n_items * sizeof(hc::BatchItemDev) + 255) / 256 * 256 + 256);
+    return (int64_t)((n_items * sizeof(hc::BatchItemDev) + 255) / 256 * 256 + 512);   // + 36 counters
 }
 
 HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg, void *d_scratch,
@@ -497,17 +506,18 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
     if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
 
-    hc::PhaseDesc phases[12];
+    hc::PhaseDesc phases[36];
     int n_phases = 0, n_dev = 0;
     for (int op = 0; op < 3; ++op) {
-        for (int kind = 0; kind < 4; ++kind) {
-            hc::PhaseDesc ph{kind, op, n_dev, 0, 0, n_phases};
+        for (int kind = 0; kind < 4; ++kind)
+        for (int bb = 32; bb <= 128; bb *= 2) {
+            hc::PhaseDesc ph{kind, op, bb, n_dev, 0, 0, n_phases};
             for (int64_t i = 0; i < n_items; ++i) {
                 const hc_batch_item &it = items[i];
                 if (!it.table || it.table->magic != HC_TABLE_MAGIC) return bfail(HC_ERR_ARG, "item with a bad table");
                 if (it.op < 0 || it.op > 2) return bfail(HC_ERR_ARG, "item with a bad op");
                 if (it.n < 0) return bfail(HC_ERR_ARG, "item with n < 0");
-                if (it.op != op || it.table->kind != kind || it.n == 0) continue;
+                if (it.op != op || it.table->kind != kind || it.table->bucket_bytes != bb || it.n == 0) continue;
                 const bool map = kind >= HC_MAP_I64_I32;
                 const int kb = kind == HC_SET_U32 ? 4 : 8;
                 if (!it.d_keys || reinterpret_cast<uintptr_t>(it.d_keys) % kb)
@@ -517,6 +527,7 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
                 hc::BatchItemDev &d = t_run_items[n_dev++];
                 d = hc::BatchItemDev{};
                 d.v = it.table->view;
+                d.v.rotate = it.n > (long long)d.v.nb ? 1 : 0;
                 d.keys = it.d_keys;
                 d.vals = map ? it.d_vals : nullptr;
                 d.out = it.d_out;
@@ -537,14 +548,14 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return bcuda(e, "reading the device");
     auto *d_items = static_cast<hc::BatchItemDev *>(d_scratch);
-    auto *d_ctr = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_scratch) + need - 256);
+    auto *d_ctr = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_scratch) + need - 512);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemcpyAsync(d_items, t_run_items, (size_t)n_dev * sizeof(hc::BatchItemDev), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return bcuda(e, "copying the batch descriptors");
-    hc::k_zero_counters<<<1, 32, 0, s>>>(d_ctr, n_phases);
+    hc::k_zero_counters<<<1, 64, 0, s>>>(d_ctr, n_phases);
     for (int p = 0; p < n_phases; ++p) {
         const hc::PhaseDesc &ph = phases[p];
-        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, lb, kpt);
+        hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, lb, kpt);
         int per_sm = c.blocks_per_sm;
         if (per_sm <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0) != cudaSuccess) per_sm = 1;
         if (per_sm <= 0) per_sm = 1;

@@ -81,6 +81,8 @@ struct View {
     unsigned long long seed;
     int hash_mode;
     int pad_from;                // slots at positions >= pad_from of the last bucket are padding
+    int rotate;                  // inserts scan a bucket from a key-dependent slot (set per call)
+    int reserved;
 };
 
 template <int KIND> struct Traits;
@@ -137,6 +139,13 @@ __device__ __forceinline__ unsigned long long teschner(unsigned long long key) {
 __device__ __forceinline__ unsigned long long first_bucket(const View &v, unsigned long long key) {
     if (v.hash_mode == HASH_TESCHNER) return teschner(key) % v.nb;
     return __umul64hi(fmix64(key ^ v.seed), v.nb);
+}
+
+// Key-dependent starting slot of an insert's scan inside a bucket of SPB
+// slots (low bits of a 64-bit mix; the bucket index uses the high bits).
+template <int SPB>
+__device__ __forceinline__ int slot_rotation(unsigned long long key) {
+    return (int)(fmix64(key ^ 0x9E3779B97F4A7C15ull) & (unsigned long long)(SPB - 1));
 }
 
 __device__ __forceinline__ unsigned long long next_bucket(const View &v, unsigned long long b) {
@@ -407,13 +416,26 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
             }
             const unsigned ge = grp.ballot(le != 0);
             if (ffb[j] == ~0ull) {               // remember the first free slot
+                // With v.rotate, slots are scanned in an order rotated by a
+                // key-dependent offset: every inserter of one key follows the
+                // same order (so equal keys still meet in one slot), while
+                // different keys aiming at one bucket spread over its free
+                // slots instead of all racing for the lowest one.  The host
+                // turns it on when a call carries more keys than the table
+                // has buckets (several inserters per bucket).
                 lt &= claimable<KIND, BB, LB>(v, b[j], grp.sub);
-                const unsigned gf = grp.ballot((le | lt) != 0);
+                const uint32_t lf = le | lt;
+                const int rot = v.rotate ? slot_rotation<Lay::SPB>(k[j]) : 0;
+                const int lo = rot - grp.sub * SPL;          // this lane's first slot at or after rot
+                const uint32_t at_or_after = lo <= 0 ? Lay::ALL : (lo >= SPL ? 0u : (Lay::ALL & ~((1u << lo) - 1u)));
+                const uint32_t f_hi = lf & at_or_after;
+                const unsigned gh = grp.ballot(f_hi != 0);
+                const unsigned gf = gh ? gh : grp.ballot(lf != 0);
                 if (gf) {
                     const int owner = __ffs(gf) - 1;
-                    const uint32_t lf = grp.bcast(le | lt, owner);
+                    const uint32_t pick = grp.bcast(gh ? f_hi : lf, owner);
                     const uint32_t lemp = grp.bcast(le, owner);
-                    const int s = __ffs(lf) - 1;
+                    const int s = __ffs(pick) - 1;
                     ffb[j] = b[j];
                     ffs_slot[j] = owner * SPL + s;
                     ff_empty[j] = (lemp >> s) & 1u;

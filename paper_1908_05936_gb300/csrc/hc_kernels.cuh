@@ -5,6 +5,7 @@
 
 #include "hc_core.cuh"
 #include "hc_internal.h"
+#include "hc_stream.cuh"
 
 namespace hc {
 
@@ -224,9 +225,31 @@ cudaError_t launch_range_shape(int op, const View &v, const void *keys, const vo
     return cudaGetLastError();
 }
 
+// Streaming lookup: each thread owns KPT keys of its block's staged chunk and
+// keeps S probes in flight (find only, one thread per key).
+template <int KIND, int BB, int KPT, int S>
+cudaError_t launch_find_stream(const View &v, const void *keys, long long n, uint8_t *out, void *vals_out, int block,
+                               cudaStream_t s) {
+    using T = Traits<KIND>;
+    const long long chunk = (long long)block * KPT;
+    const unsigned grid = (unsigned)((n + chunk - 1) / chunk);
+    const size_t smem = (size_t)chunk * (sizeof(typename T::Key) + sizeof(typename T::Val) + 1);
+    k_find_stream<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys, n, out,
+                                                              (typename T::Val *)vals_out);
+    return cudaGetLastError();
+}
+
 template <int KIND, int BB, int LB>
 cudaError_t launch_range_kpt(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
                              void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
+    if (sh.keys_per_group >= 4) {
+        if constexpr (LB == Slots<KIND, BB>::KRB) {
+            if (op != OP_FIND || n <= 0) return n <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+            if (sh.keys_per_group == 4) return launch_find_stream<KIND, BB, 4, 2>(v, keys, n, out, vals_out, sh.block, s);
+            if (sh.keys_per_group == 8) return launch_find_stream<KIND, BB, 8, 4>(v, keys, n, out, vals_out, sh.block, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (sh.keys_per_group) {
         case 1: return launch_range_shape<KIND, BB, LB, 1>(op, v, keys, vals, n, out, vals_out, sh, skip, s);
         case 2: return launch_range_shape<KIND, BB, LB, 2>(op, v, keys, vals, n, out, vals_out, sh, skip, s);

@@ -76,11 +76,14 @@ def _time_once(fn) -> float:
 
 
 def candidates(table: Table) -> list[dict]:
-    default = table.get_launch(0)["lane_bytes"]          # the bucket's key region
-    lanes = [lb for lb in LANES if lb <= default and (lb >= 32 or table.is_map)]
+    krb = table.get_launch(0)["lane_bytes"]              # the bucket's key region
+    lanes = [lb for lb in LANES if lb <= krb and (lb >= 32 or table.is_map)]
     if table.is_map:
         lanes.append(table.bucket_bytes)                  # keys and values in one read
-    return [dict(lane_bytes=lb, keys_per_group=k, block=b) for lb in lanes for k in KEYS_IN_FLIGHT for b in BLOCKS]
+    out = [dict(lane_bytes=lb, keys_per_group=k, block=b) for lb in lanes for k in KEYS_IN_FLIGHT for b in BLOCKS]
+    # streaming lookups (find only): one thread per key over the key region
+    out += [dict(lane_bytes=krb, keys_per_group=k, block=b) for k in (4, 8) for b in BLOCKS]
+    return out
 
 
 def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0.8) -> dict:
@@ -102,8 +105,11 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
     results = {"insert": [], "find_hit": [], "find_miss": [], "erase": []}
     t.insert(last, last_v, status=False)                  # the table starts at the target load factor
     for c in candidates(t):
-        for op in (0, 1, 2):
-            t.set_launch(op, fold=2, **c)
+        streaming = c["keys_per_group"] > 2
+        t.set_launch(L.OP_FIND, fold=2, **c)
+        if not streaming:
+            t.set_launch(L.OP_INSERT, fold=2, **c)
+            t.set_launch(L.OP_ERASE, fold=2, **c)
 
         def ins():
             t.insert(last, last_v, status=out)
@@ -113,12 +119,13 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
 
         # erase / re-insert the last batch: each insert stores new keys into a
         # table at the target load factor, each erase removes present keys
-        e_ms, i_ms = [], []
-        for _ in range(2):
-            e_ms.append(_time_once(era))
-            i_ms.append(_time_once(ins))
-        results["insert"].append((min(i_ms), c))
-        results["erase"].append((min(e_ms), c))
+        if not streaming:
+            e_ms, i_ms = [], []
+            for _ in range(2):
+                e_ms.append(_time_once(era))
+                i_ms.append(_time_once(ins))
+            results["insert"].append((min(i_ms), c))
+            results["erase"].append((min(e_ms), c))
         results["find_hit"].append((_time(lambda: t.find(hit, found=out, vals_out=vout)), c))
         results["find_miss"].append((_time(lambda: t.find(miss, found=out, vals_out=vout)), c))
     t.close()

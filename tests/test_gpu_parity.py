@@ -258,3 +258,27 @@ def test_host_buffer_calls(kind):
         p.check()
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("bb", (32, 64, 128))
+@pytest.mark.parametrize("kpt", (4, 8))
+def test_streaming_find(kind, bb, kpt):
+    """Streaming lookup (keys staged per block, several probes in flight per
+    thread, refilled as they finish) against the oracle, with side-slot keys,
+    duplicates, ragged chunk tails, absent and erased keys."""
+    rng = np.random.default_rng(bb + kpt + kind)
+    p = Pair(kind, 20000, bucket_bytes=bb)
+    krb = p.g.get_launch(0)["lane_bytes"]
+    p.g.set_launch(1, lane_bytes=krb, keys_per_group=kpt, block=96)
+    try:
+        keys = random_keys(kind, 15000, rng)
+        keys = np.concatenate([keys, np.array(RESERVED[kind])])
+        p.insert(keys, value_for(kind, keys))
+        p.erase(keys[::5])
+        for n in (0, 1, 95, 96, 97, 96 * kpt + 1, 40001):
+            q = np.concatenate([keys, random_keys(kind, 30000, rng)])[rng.integers(0, 45002, size=n)]
+            p.find(q)
+        p.check()
+    finally:
+        p.close()
