@@ -278,7 +278,9 @@ def run_gpu(args, rank: int, world: int):
         "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded splitmix64 keys)",
         "config": {"workload": wl.name, "slots": wl.slots, "batch": B, "load_factor": args.lf,
-                   "bucket_bytes": bb, "launch": t.get_launch(1), "l2": "inputs larger than L2 (4 GiB table)",
+                   "bucket_bytes": bb,
+                   "launch": {op: t.get_launch(i) for i, op in enumerate(("insert", "find", "erase"))},
+                   "l2": "inputs larger than L2 (4 GiB table)",
                    "parallelism": f"replicas{world}"},
         "ops": {k: ({kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
                     if isinstance(v, dict) else v) for k, v in summary.items()},

@@ -107,15 +107,17 @@ typedef struct hc_config {
  * lanes probes a bucket together (lane_bytes == bucket_bytes: one thread per
  * key); each group handles keys_per_group keys at once so that several
  * bucket reads are in flight per lane.  Zero fields keep the current value.
- * keys_per_group 4 or 8 (find only, lane_bytes = the key region) selects the
- * streaming lookup: a block stages its keys in shared memory and each thread
- * keeps 2 or 4 probes in flight, refilling as they finish.  Defaults:
- * lane_bytes = the bucket's key region (one thread per key), keys_per_group 1
- * (4 for map lookups), block 64, folding off.  Results never depend on the
+ * keys_per_group 4 or 8 (any operation, lane_bytes = the key region)
+ * selects the streaming form: a block stages its keys in shared memory and
+ * each thread keeps 2 or 4 probes in flight, refilling as they finish (no
+ * duplicate folding in this form).  Defaults:
+ * lane_bytes = the bucket's key region (one thread per key), block 64,
+ * folding off; keys_per_group 4 for inserts, 8 for erases, 4 for map lookups
+ * and 1 for set lookups.  Results never depend on the
  * shape. */
 typedef struct hc_launch {
     int32_t lane_bytes;       /* 32, 64 or 128, at most bucket_bytes     */
-    int32_t keys_per_group;   /* 1 or 2; 4 or 8: streaming find          */
+    int32_t keys_per_group;   /* 1 or 2; 4 or 8: streaming forms       */
     int32_t block;            /* threads per block: 64..256, multiple of 32  */
     int32_t fold_duplicates;  /* 1: equal keys inside a warp are folded to
                                  one probe (__match_any_sync); 2: off      */

@@ -303,10 +303,13 @@ hc_rc hc_create(hc_table **out, int32_t kind, int64_t slots, const hc_config *cf
         return fail(HC_ERR_OOM, "cudaMalloc of %lld bytes failed: %s", (long long)g.bytes, cudaGetErrorString(e));
     }
     t->view = make_view(t->d_mem, g, seed, hm);
-    // one thread per key reading the bucket's keys, one key in flight,
-    // 64-thread blocks: the best shape of the sweeps on GB300 for uniform keys
+    // one thread per key reading the bucket's keys, 64-thread blocks: the
+    // best shapes of the sweeps on GB300 for uniform keys.  Inserts stream 4
+    // keys per thread (2 in flight), erases 8 (4 in flight), map lookups 4;
+    // set lookups run one key per thread in lock step.
     for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{key_region_bytes(kind, bb), 1, 64, 0, 0};
-    // maps look up with the streaming kernel: 4 keys per thread, 2 in flight
+    t->shape[hc::OP_INSERT].keys_per_group = 4;
+    t->shape[hc::OP_ERASE].keys_per_group = 8;
     if (is_map(kind)) t->shape[hc::OP_FIND].keys_per_group = 4;
     e = dispatch_clear(t, t->view, t->phys, t->capacity, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
@@ -355,8 +358,9 @@ hc_rc hc_set_launch(hc_table *t, int32_t op, const hc_launch *shape) {
                     "lane_bytes must be 32, 64 or 128 (16 for maps) and at most the %d-byte key region, or the whole "
                     "bucket for maps", krb);
     if (sh.keys_per_group != 1 && sh.keys_per_group != 2 &&
-        !((sh.keys_per_group == 4 || sh.keys_per_group == 8) && op == hc::OP_FIND && sh.lane_bytes == krb))
-        return fail(HC_ERR_ARG, "keys_per_group must be 1 or 2 (4 or 8: streaming find, lane = key region)");
+        !((sh.keys_per_group == 4 || sh.keys_per_group == 8) && sh.lane_bytes == krb))
+        return fail(HC_ERR_ARG,
+                    "keys_per_group must be 1 or 2 (4 or 8: streaming, lane = the key region)");
     if (sh.block < 64 || sh.block > 256 || sh.block % 32)
         return fail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     t->shape[op] = sh;

@@ -239,14 +239,44 @@ cudaError_t launch_find_stream(const View &v, const void *keys, long long n, uin
     return cudaGetLastError();
 }
 
+template <int KIND, int BB, int KPT, int S>
+cudaError_t launch_insert_stream(const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
+                                 const uint8_t *skip, int block, cudaStream_t s) {
+    using T = Traits<KIND>;
+    const long long chunk = (long long)block * KPT;
+    const unsigned grid = (unsigned)((n + chunk - 1) / chunk);
+    const size_t smem = (size_t)chunk * (sizeof(typename T::Key) + sizeof(typename T::Val) + 1);
+    k_insert_stream<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys,
+                                                                (const typename T::Val *)vals, n, out, skip);
+    return cudaGetLastError();
+}
+
+template <int KIND, int BB, int KPT, int S>
+cudaError_t launch_erase_stream(const View &v, const void *keys, long long n, uint8_t *out, int block, cudaStream_t s) {
+    using T = Traits<KIND>;
+    const long long chunk = (long long)block * KPT;
+    const unsigned grid = (unsigned)((n + chunk - 1) / chunk);
+    const size_t smem = (size_t)chunk * (sizeof(typename T::Key) + 1);
+    k_erase_stream<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys, n, out);
+    return cudaGetLastError();
+}
+
 template <int KIND, int BB, int LB>
 cudaError_t launch_range_kpt(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
                              void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
-    if (sh.keys_per_group >= 4) {
+    if (sh.keys_per_group >= 4) {       // streaming forms: one thread per key
         if constexpr (LB == Slots<KIND, BB>::KRB) {
-            if (op != OP_FIND || n <= 0) return n <= 0 ? cudaSuccess : cudaErrorInvalidValue;
-            if (sh.keys_per_group == 4) return launch_find_stream<KIND, BB, 4, 2>(v, keys, n, out, vals_out, sh.block, s);
-            if (sh.keys_per_group == 8) return launch_find_stream<KIND, BB, 8, 4>(v, keys, n, out, vals_out, sh.block, s);
+            if (n <= 0) return cudaSuccess;
+            if (op == OP_FIND) {
+                if (sh.keys_per_group == 4) return launch_find_stream<KIND, BB, 4, 2>(v, keys, n, out, vals_out, sh.block, s);
+                if (sh.keys_per_group == 8) return launch_find_stream<KIND, BB, 8, 4>(v, keys, n, out, vals_out, sh.block, s);
+            } else if (op == OP_INSERT) {
+                if (sh.keys_per_group == 4) return launch_insert_stream<KIND, BB, 4, 2>(v, keys, vals, n, out, skip, sh.block, s);
+                if (sh.keys_per_group == 8) return launch_insert_stream<KIND, BB, 8, 4>(v, keys, vals, n, out, skip, sh.block, s);
+            } else {
+                if (sh.keys_per_group == 4) return launch_erase_stream<KIND, BB, 4, 2>(v, keys, n, out, sh.block, s);
+                if (sh.keys_per_group == 8) return launch_erase_stream<KIND, BB, 8, 4>(v, keys, n, out, sh.block, s);
+            }
         }
         return cudaErrorInvalidValue;
     }

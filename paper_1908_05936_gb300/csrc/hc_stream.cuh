@@ -103,4 +103,271 @@ k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8
     }
 }
 
+// Streaming insert: the same staging and refilling as k_find_stream.  Within
+// one round every slot first decides whether it claims, then all claiming
+// slots issue their compare-and-swap together, so the atomics of different
+// keys overlap.  Statuses collect in shared memory and leave in coalesced
+// stores; counters leave with one atomic per warp.  Equal keys inside a warp
+// are not folded here (folding is a lock-step option).
+template <int KIND, int BB, int KPT, int S>
+__global__ void __launch_bounds__(256)
+k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
+                uint8_t *status, const uint8_t *skip) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    using Val = typename T::Val;
+    using Sl = Slots<KIND, BB>;
+    using Lay = Layout<KIND, BB, Sl::KRB>;
+    constexpr int LB = Sl::KRB;
+    constexpr int SPL = Sl::SPB;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nt = blockDim.x;
+    const int chunk = nt * KPT;
+    Key *sk = reinterpret_cast<Key *>(smem);
+    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * sizeof(Key));
+    uint8_t *ss = smem + (size_t)chunk * (sizeof(Key) + sizeof(Val));
+
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    for (int i = threadIdx.x; i < m; i += nt) {
+        sk[i] = ld_stream(keys + c0 + i);
+        if constexpr (T::MAP) sv[i] = ld_stream(vals + c0 + i);
+        ss[i] = (skip && ld_stream(skip + c0 + i)) ? (uint8_t)ST_EXISTS : (uint8_t)0xFF;   // 0xFF: to do
+    }
+    __syncthreads();
+
+    Counts cnt;
+    int idx[S];
+    Key key[S];
+    unsigned long long b[S], ffb[S];
+    uint32_t probes[S], restarts[S], ffs_slot[S];
+    bool ff_empty[S];
+    int next = 0;
+    uint32_t active = 0;
+    auto take = [&](int s) {
+        while (next < KPT) {
+            const int i = threadIdx.x + (next++) * nt;
+            if (i >= m) { next = KPT; break; }
+            if (ss[i] != 0xFF) continue;                       // reported present by a find
+            const Key k = sk[i];
+            const int side = side_index<KIND>(k);
+            if (side >= 0) {                                   // key equal to a marker: side slot
+                const bool won = atomicCAS(&v.hdr->side_present[side], 0u, 1u) == 0u;
+                if (won) {
+                    if constexpr (T::MAP) v.hdr->side_val[side] = (unsigned long long)sv[i];
+                    ++cnt.ins;
+                }
+                ss[i] = won ? (uint8_t)ST_INSERTED : (uint8_t)ST_EXISTS;
+                continue;
+            }
+            idx[s] = i;
+            key[s] = k;
+            b[s] = first_bucket(v, (unsigned long long)k);
+            probes[s] = 0;
+            restarts[s] = 0;
+            ffb[s] = ~0ull;
+            active |= 1u << s;
+            return;
+        }
+    };
+#pragma unroll
+    for (int s = 0; s < S; ++s) take(s);
+    while (active) {
+        LaneWords<LB> lw[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (active >> s & 1u) lw[s].load(v.buckets + b[s] * BB);
+        uint32_t claiming = 0;
+        uint32_t finished = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!(active >> s & 1u)) continue;
+            uint32_t lm = 0, le = 0, lt = 0;
+#pragma unroll
+            for (int q = 0; q < SPL; ++q) {
+                const Key ks = slot_key<KIND, LB>(lw[s], q);
+                lm |= (uint32_t)(ks == key[s]) << q;
+                le |= (uint32_t)(ks == T::EMPTY) << q;
+                lt |= (uint32_t)(ks == T::TOMB) << q;
+            }
+            if (lm) {                                           // already stored
+                ss[idx[s]] = ST_EXISTS;
+                finished |= 1u << s;
+                continue;
+            }
+            if (ffb[s] == ~0ull) {                              // first free slot, rotated scan
+                lt &= claimable<KIND, BB, LB>(v, b[s], 0);
+                const uint32_t lf = le | lt;
+                if (lf) {
+                    const int rot = v.rotate ? slot_rotation<Lay::SPB>(key[s]) : 0;
+                    const uint32_t hi = lf & (Lay::ALL & ~((1u << rot) - 1u));
+                    const int q = __ffs(hi ? hi : lf) - 1;
+                    ffb[s] = b[s];
+                    ffs_slot[s] = q;
+                    ff_empty[s] = (le >> q) & 1u;
+                }
+            }
+            if (le) {
+                claiming |= 1u << s;
+            } else if (++probes[s] >= v.nb) {
+                if (ffb[s] == ~0ull) {                          // no free slot anywhere
+                    ss[idx[s]] = ST_OVERFLOW;
+                    cnt.over = 1;
+                    finished |= 1u << s;
+                } else {
+                    claiming |= 1u << s;                        // only tombstones were free
+                }
+            } else {
+                b[s] = next_bucket(v, b[s]);
+            }
+        }
+        Key old[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (claiming >> s & 1u)
+                old[s] = cas_key<KIND>(Slots<KIND, BB>::key(v, ffb[s], ffs_slot[s]), ff_empty[s] ? T::EMPTY : T::TOMB,
+                                       key[s]);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!(claiming >> s & 1u)) continue;
+            const Key expect = ff_empty[s] ? T::EMPTY : T::TOMB;
+            if (old[s] == expect) {
+                if constexpr (T::MAP) store_val<KIND, BB>(v, ffb[s], ffs_slot[s], (unsigned long long)sv[idx[s]]);
+                ss[idx[s]] = ST_INSERTED;
+                ++cnt.ins;
+                cnt.new_slot += ff_empty[s] ? 1u : 0u;
+                finished |= 1u << s;
+            } else if (old[s] == key[s]) {
+                ss[idx[s]] = ST_EXISTS;                         // an equal key won the race
+                finished |= 1u << s;
+            } else if (++restarts[s] > kMaxRestarts) {
+                atomicOr(&v.hdr->err, ERR_PROBE_BOUND);
+                ss[idx[s]] = ST_OVERFLOW;
+                cnt.over = 1;
+                finished |= 1u << s;
+            } else {                                            // lost the slot to another key
+                b[s] = first_bucket(v, (unsigned long long)key[s]);
+                probes[s] = 0;
+                ffb[s] = ~0ull;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (finished >> s & 1u) {
+                active &= ~(1u << s);
+                take(s);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += nt)
+        if (status) st_stream(status + c0 + i, ss[i]);
+    flush_counts(v, cnt);
+}
+
+// Streaming erase: the staging and refilling of k_find_stream; a slot that
+// finds its key joins the round's compare-and-swap (key -> TOMB) with the
+// other slots that found theirs.  A failed swap means an equal key of the
+// same call erased the slot first: that key reports ERASED, this one
+// NOT_FOUND, as in the lock-step form.
+template <int KIND, int BB, int KPT, int S>
+__global__ void __launch_bounds__(256)
+k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    using Sl = Slots<KIND, BB>;
+    constexpr int LB = Sl::KRB;
+    constexpr int SPL = Sl::SPB;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nt = blockDim.x;
+    const int chunk = nt * KPT;
+    Key *sk = reinterpret_cast<Key *>(smem);
+    uint8_t *ss = smem + (size_t)chunk * sizeof(Key);
+
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    for (int i = threadIdx.x; i < m; i += nt) sk[i] = ld_stream(keys + c0 + i);
+    __syncthreads();
+
+    Counts cnt;
+    int idx[S];
+    Key key[S];
+    unsigned long long b[S];
+    uint32_t probes[S], hit_slot[S];
+    int next = 0;
+    uint32_t active = 0;
+    auto take = [&](int s) {
+        while (next < KPT) {
+            const int i = threadIdx.x + (next++) * nt;
+            if (i >= m) { next = KPT; break; }
+            const Key k = sk[i];
+            const int side = side_index<KIND>(k);
+            if (side >= 0) {                                   // key equal to a marker: side slot
+                const bool won = atomicCAS(&v.hdr->side_present[side], 1u, 0u) == 1u;
+                cnt.del += won ? 1u : 0u;
+                ss[i] = won ? (uint8_t)ST_ERASED : (uint8_t)ST_NOT_FOUND;
+                continue;
+            }
+            idx[s] = i;
+            key[s] = k;
+            b[s] = first_bucket(v, (unsigned long long)k);
+            probes[s] = 0;
+            active |= 1u << s;
+            return;
+        }
+    };
+#pragma unroll
+    for (int s = 0; s < S; ++s) take(s);
+    while (active) {
+        LaneWords<LB> lw[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (active >> s & 1u) lw[s].load(v.buckets + b[s] * BB);
+        uint32_t hitting = 0, finished = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!(active >> s & 1u)) continue;
+            uint32_t lm = 0, le = 0;
+#pragma unroll
+            for (int q = 0; q < SPL; ++q) {
+                const Key ks = slot_key<KIND, LB>(lw[s], q);
+                lm |= (uint32_t)(ks == key[s]) << q;
+                le |= (uint32_t)(ks == T::EMPTY) << q;
+            }
+            if (lm) {
+                hit_slot[s] = __ffs(lm) - 1;
+                hitting |= 1u << s;
+            } else if (le || ++probes[s] >= v.nb) {
+                ss[idx[s]] = ST_NOT_FOUND;
+                finished |= 1u << s;
+            } else {
+                b[s] = next_bucket(v, b[s]);
+            }
+        }
+        Key old[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (hitting >> s & 1u) old[s] = cas_key<KIND>(Sl::key(v, b[s], hit_slot[s]), key[s], T::TOMB);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!(hitting >> s & 1u)) continue;
+            const bool won = old[s] == key[s];
+            ss[idx[s]] = won ? (uint8_t)ST_ERASED : (uint8_t)ST_NOT_FOUND;
+            cnt.del += won ? 1u : 0u;
+            finished |= 1u << s;
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (finished >> s & 1u) {
+                active &= ~(1u << s);
+                take(s);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += nt)
+        if (status) st_stream(status + c0 + i, ss[i]);
+    flush_counts(v, cnt);
+}
+
 }  // namespace hc

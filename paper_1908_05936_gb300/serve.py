@@ -71,6 +71,8 @@ class _Slot:
     h_in: torch.Tensor           # pinned host staging of inputs
     h_out: torch.Tensor          # pinned host staging of results
     desc: torch.Tensor           # device descriptors for hc_batch_run
+    items: ctypes.Array          # host descriptors, reused by every launch of the slot
+    done_event: torch.cuda.Event # reused completion event
     event: torch.cuda.Event | None = None
     reqs: list = field(default_factory=list)
     layout: list = field(default_factory=list)
@@ -94,7 +96,8 @@ class Server:
                 self.slots.append(_Slot(lane, torch.empty(slot_bytes, dtype=torch.uint8, device="cuda"),
                                         torch.empty(slot_bytes, dtype=torch.uint8, pin_memory=True),
                                         torch.empty(slot_bytes, dtype=torch.uint8, pin_memory=True),
-                                        torch.empty(desc_bytes, dtype=torch.uint8, device="cuda")))
+                                        torch.empty(desc_bytes, dtype=torch.uint8, device="cuda"),
+                                        (L.BatchItem * max_items)(), torch.cuda.Event()))
         self.slot_bytes = slot_bytes
         self.resident_bytes = sum(t.stats()["table_bytes"] for t in tables)
 
@@ -153,7 +156,7 @@ class Server:
             for doff, ht in direct:
                 nb = ht.numel() * ht.element_size()
                 d[doff:doff + nb].copy_(ht.view(torch.uint8), non_blocking=True)
-            items = (L.BatchItem * len(reqs))()
+            items = slot.items
             base = d.data_ptr()
             for i, r in enumerate(reqs):
                 t = self.tables[r.table]
@@ -166,7 +169,7 @@ class Server:
                                               slot.desc.numel(), s.cuda_stream))
             else:
                 h = s.cuda_stream
-                for it in items:
+                for it in items[:len(reqs)]:
                     if it.op == L.OP_INSERT:
                         L.check(self.lib.hc_insert(it.table, it.d_keys, it.d_vals, it.n, it.d_out, h))
                     elif it.op == L.OP_FIND:
@@ -174,7 +177,7 @@ class Server:
                     else:
                         L.check(self.lib.hc_erase(it.table, it.d_keys, it.n, it.d_out, h))
             slot.h_out[:out_total].copy_(d[out_off:out_off + out_total], non_blocking=True)
-            ev = torch.cuda.Event()
+            ev = slot.done_event
             ev.record(s)
         slot.event = ev
         slot.reqs = reqs

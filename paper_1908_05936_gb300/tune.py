@@ -81,12 +81,14 @@ def candidates(table: Table) -> list[dict]:
     if table.is_map:
         lanes.append(table.bucket_bytes)                  # keys and values in one read
     out = [dict(lane_bytes=lb, keys_per_group=k, block=b) for lb in lanes for k in KEYS_IN_FLIGHT for b in BLOCKS]
-    # streaming lookups (find only): one thread per key over the key region
+    # streaming forms: one thread per key over the key region, probes refilled as they finish
     out += [dict(lane_bytes=krb, keys_per_group=k, block=b) for k in (4, 8) for b in BLOCKS]
     return out
 
 
-def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0.8) -> dict:
+def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0.8, every: list | None = None) -> dict:
+    """Best shape per operation; with `every` given, each candidate's timings
+    are appended to it as well."""
     slots = 1 << slots_log2
     n_fill = int(lf * slots)
     batch = 1 << (slots_log2 - 2)
@@ -105,11 +107,8 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
     results = {"insert": [], "find_hit": [], "find_miss": [], "erase": []}
     t.insert(last, last_v, status=False)                  # the table starts at the target load factor
     for c in candidates(t):
-        streaming = c["keys_per_group"] > 2
-        t.set_launch(L.OP_FIND, fold=2, **c)
-        if not streaming:
-            t.set_launch(L.OP_INSERT, fold=2, **c)
-            t.set_launch(L.OP_ERASE, fold=2, **c)
+        for op in (L.OP_INSERT, L.OP_FIND, L.OP_ERASE):
+            t.set_launch(op, fold=2, **c)
 
         def ins():
             t.insert(last, last_v, status=out)
@@ -119,16 +118,21 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
 
         # erase / re-insert the last batch: each insert stores new keys into a
         # table at the target load factor, each erase removes present keys
-        if not streaming:
-            e_ms, i_ms = [], []
-            for _ in range(2):
-                e_ms.append(_time_once(era))
-                i_ms.append(_time_once(ins))
-            results["insert"].append((min(i_ms), c))
-            results["erase"].append((min(e_ms), c))
+        e_ms, i_ms = [], []
+        for _ in range(2):
+            e_ms.append(_time_once(era))
+            i_ms.append(_time_once(ins))
+        results["insert"].append((min(i_ms), c))
+        results["erase"].append((min(e_ms), c))
         results["find_hit"].append((_time(lambda: t.find(hit, found=out, vals_out=vout)), c))
         results["find_miss"].append((_time(lambda: t.find(miss, found=out, vals_out=vout)), c))
     t.close()
+    if every is not None:
+        for i, (_, c) in enumerate(results["find_hit"]):
+            row = dict(c, bucket_bytes=bucket_bytes, kind=kind)
+            for op, lst in results.items():
+                row[op + "_mops"] = round(batch / lst[i][0] / 1e3, 1)
+            every.append(row)
     best = {}
     for op, lst in results.items():
         ms, c = min(lst, key=lambda x: x[0])
@@ -136,12 +140,15 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
     return best
 
 
-def tune(kinds: list[int], buckets=(32, 64, 128), slots_log2: int = 26) -> dict:
+def tune(kinds: list[int], buckets=(32, 64, 128), slots_log2: int = 26, save: bool = True,
+         every: list | None = None) -> dict:
     res = {}
     for kind in kinds:
         name = [k for k, v in KIND_NAMES.items() if v == kind][0]
         for bb in buckets:
-            res[f"{name}/{bb}"] = tune_table(kind, bb, slots_log2)
+            res[f"{name}/{bb}"] = tune_table(kind, bb, slots_log2, every=every)
+    if not save:
+        return res
     cache = {}
     if os.path.exists(CACHE):
         with open(CACHE) as f:
@@ -174,11 +181,17 @@ def main():
     ap.add_argument("--kinds", default="map_u64_u64,set_u64,set_u32,map_i64_i32")
     ap.add_argument("--buckets", default="32,64,128")
     ap.add_argument("--slots-log2", type=int, default=26)
+    ap.add_argument("--all", action="store_true", help="also print every candidate's rates, one JSON line each")
+    ap.add_argument("--no-save", action="store_true", help="leave the cache file unchanged")
     a = ap.parse_args()
     from . import build
     build.build()
     kinds = [KIND_NAMES[k] for k in a.kinds.split(",")]
-    print(json.dumps(tune(kinds, tuple(int(b) for b in a.buckets.split(",")), a.slots_log2)))
+    every = [] if a.all else None
+    best = tune(kinds, tuple(int(b) for b in a.buckets.split(",")), a.slots_log2, save=not a.no_save, every=every)
+    for row in every or []:
+        print(json.dumps(row))
+    print(json.dumps(best))
 
 
 if __name__ == "__main__":

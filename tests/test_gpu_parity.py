@@ -8,6 +8,7 @@ import torch
 
 import compare as C
 from gpu_pair import RESERVED, Pair, random_keys, value_for
+from paper_1908_05936_gb300.table import to_device, to_numpy
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -279,6 +280,76 @@ def test_streaming_find(kind, bb, kpt):
         for n in (0, 1, 95, 96, 97, 96 * kpt + 1, 40001):
             q = np.concatenate([keys, random_keys(kind, 30000, rng)])[rng.integers(0, 45002, size=n)]
             p.find(q)
+        p.check()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("bb", (32, 64, 128))
+@pytest.mark.parametrize("kpt", (4, 8))
+def test_streaming_insert(kind, bb, kpt):
+    """Streaming insert against the oracle: duplicates inside a batch,
+    side-slot keys, tombstone reuse after erases, ragged chunk tails, the
+    find-then-insert skip path, and overflow of a small table (invariants)."""
+    rng = np.random.default_rng(100 + bb + kpt + kind)
+    p = Pair(kind, 6000, bucket_bytes=bb)
+    krb = p.g.get_launch(0)["lane_bytes"]
+    p.g.set_launch(0, lane_bytes=krb, keys_per_group=kpt, block=64)
+    dom = np.concatenate([random_keys(kind, 5000, rng), np.array(RESERVED[kind])])
+    try:
+        for b, n in enumerate((0, 1, 63, 64, 65, 64 * kpt + 3, 3000, 3000)):
+            keys = dom[rng.integers(0, len(dom), size=n)]
+            p.insert(keys, value_for(kind, keys, salt=b))
+            p.erase(keys[::3])
+        p.check()
+        # find-then-insert: flagged keys are EXISTS without a probe
+        keys = dom[rng.integers(0, len(dom), size=4000)]
+        dk = to_device(keys)
+        f, _ = p.g.find(dk, vals_out=False)
+        st = to_numpy(p.g.insert_if_absent(dk, to_device(value_for(kind, keys)) if p.is_map else None, f), np.uint8)
+        of, _ = p.o.find(keys)
+        ost = np.full(len(keys), C.EXISTS, np.uint8)
+        miss = np.nonzero(of == 0)[0]
+        ost[miss] = p.o.insert(keys[miss], value_for(kind, keys)[miss] if p.is_map else None)
+        C.assert_status(keys, st, ost, "insert_if_absent")
+        p.check()
+    finally:
+        p.close()
+    # overflow: a table of 100 slots takes 100 regular keys, the rest overflow
+    q = Pair(kind, 100, bucket_bytes=bb)
+    q.g.set_launch(0, lane_bytes=krb, keys_per_group=kpt, block=64)
+    try:
+        keys = random_keys(kind, 300, rng)
+        gs, _ = q.insert(keys, value_for(kind, keys), check=False)
+        gk, _ = q.g.dump_numpy()
+        C.check_overflow_insert(keys, gs, set(), 100, {int(x) for x in C.bits(gk)}, set())
+    finally:
+        q.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("bb", (32, 64, 128))
+@pytest.mark.parametrize("kpt", (4, 8))
+def test_streaming_erase(kind, bb, kpt):
+    """Streaming erase against the oracle, with streaming insert and find on
+    the same table: equal keys inside one erase call (one ERASED, the rest
+    NOT_FOUND), side-slot keys, absent and already erased keys, ragged chunk
+    tails, and re-inserts into the freed tombstones."""
+    rng = np.random.default_rng(300 + bb + kpt + kind)
+    p = Pair(kind, 8000, bucket_bytes=bb)
+    krb = p.g.get_launch(0)["lane_bytes"]
+    for op in (0, 1, 2):
+        p.g.set_launch(op, lane_bytes=krb, keys_per_group=kpt, block=128)
+    dom = np.concatenate([random_keys(kind, 7000, rng), np.array(RESERVED[kind])])
+    try:
+        p.insert(dom[:6000], value_for(kind, dom[:6000]))
+        for b, n in enumerate((0, 1, 127, 128, 129, 128 * kpt + 5, 2500, 5000)):
+            keys = dom[rng.integers(0, len(dom), size=n)]
+            p.erase(keys)
+            p.find(dom[rng.integers(0, len(dom), size=1000)])
+            back = dom[rng.integers(0, len(dom), size=n // 2)]
+            p.insert(back, value_for(kind, back, salt=b))
         p.check()
     finally:
         p.close()
