@@ -33,6 +33,22 @@ METRIC = "Mops/s insert/find/erase at LF 0.8; p50/p99 batch latency; % of HBM pe
 # algorithmic bytes per op for map<u64,u64>: one 32-byte slot sector read
 # (+ one written for modifying ops) + key/value in + status/value out
 BYTES_PER_OP = {"insert": 16 + 1 + 32 + 32, "find": 8 + 8 + 1 + 32, "erase": 8 + 1 + 32 + 32}
+# DRAM bytes per op of the range insert kernel (k_insert_stream<map<u64,u64>,
+# 64-byte buckets, 4 keys/thread, 2 in flight>, 64-thread blocks) on this
+# workload: dram__bytes_read.sum + dram__bytes_write.sum over the four fill
+# launches of one step at full size (one ncu capture), divided by the keys
+# they inserted.  Valid only while the kernel sources hash to `digest`.
+INSERT_TRAFFIC = {"bytes_per_op": 227.69, "digest": "1f161a0504b21e1e",
+                  "sources": ("hc_core.cuh", "hc_stream.cuh", "hc_kernels.cuh")}
+
+
+def kernel_digest(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1908_05936_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -51,7 +67,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=24)
-    ap.add_argument("--workload", default="map_sweep", choices=["map_sweep", "multi_table", "served", "rgbd", "set_u32"])
+    ap.add_argument("--workload", default="map_sweep",
+                    choices=["map_sweep", "device_api", "multi_table", "served", "rgbd", "set_u32"])
     ap.add_argument("--rgbd-slots", type=int, default=12_500_000)
     ap.add_argument("--rgbd-hash", type=int, default=1, help="1 = the paper's spatial hash, 0 = mix64")
     ap.add_argument("--tables", type=int, default=1024)
@@ -185,6 +202,32 @@ def run_gpu(args, rank: int, world: int):
         t.set_launch(op, lane_bytes=args.lane_bytes, keys_per_group=args.kpt, block=args.block)
     stream = torch.cuda.current_stream()
     calls = []   # (name, n, start_event, end_event)
+    in_kernel = args.workload == "device_api"
+    if in_kernel:
+        # the same step through a user kernel calling the in-kernel function
+        # form, one operation per thread (examples/device_api.cu)
+        from paper_1908_05936_gb300 import device_api as D
+        build.build_examples()
+        dv = t.device_view()
+        blk = args.block or 128
+
+        def do_insert(k, v, st):
+            D.apply(t, k, L.OP_INSERT, vals=v, status=st, block=blk, view=dv)
+
+        def do_find(k, f, vo):
+            D.apply(t, k, L.OP_FIND, status=f, vals_out=vo, block=blk, view=dv)
+
+        def do_erase(k, st):
+            D.apply(t, k, L.OP_ERASE, status=st, block=blk, view=dv)
+    else:
+        def do_insert(k, v, st):
+            t.insert(k, v, status=st)
+
+        def do_find(k, f, vo):
+            t.find(k, found=f, vals_out=vo)
+
+        def do_erase(k, st):
+            t.erase(k, status=st)
 
     def ev():
         e = torch.cuda.Event(enable_timing=True)
@@ -200,19 +243,19 @@ def run_gpu(args, rank: int, world: int):
         for off in range(0, wl.n_fill, B):
             n = min(B, wl.n_fill - off)
             a = ev()
-            t.insert(d_fill[off:off + n], d_vals[off:off + n], status=st_buf[:n])
+            do_insert(d_fill[off:off + n], d_vals[off:off + n], st_buf[:n])
             b = ev()
             rec.append(("insert", n, a, b))
         a = ev()
-        t.find(d_hit, found=found, vals_out=vout)
+        do_find(d_hit, found, vout)
         b = ev()
         rec.append(("find_hit", B, a, b))
         a = ev()
-        t.find(d_miss, found=found, vals_out=vout)
+        do_find(d_miss, found, vout)
         b = ev()
         rec.append(("find_miss", B, a, b))
         a = ev()
-        t.erase(d_er, status=st_buf)
+        do_erase(d_er, st_buf)
         b = ev()
         rec.append(("erase", B, a, b))
         if record:
@@ -270,6 +313,10 @@ def run_gpu(args, rank: int, world: int):
     dom_n = sum(x[0] for x in per[dom]) / len(per[dom])
     dom_ms = summary[dom]["ms_total"] / len(per[dom])
     achieved = BYTES_PER_OP[kinds[dom]] * dom_n / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    if (dom == "insert" and not in_kernel and bb == 64 and t.get_launch(0)["keys_per_group"] == 4
+            and t.get_launch(0)["block"] == 64 and kernel_digest(INSERT_TRAFFIC["sources"]) == INSERT_TRAFFIC["digest"]):
+        traffic = INSERT_TRAFFIC["bytes_per_op"] * dom_n      # DRAM bytes per launch
     peak, peak_src = hbm_peak()
     ceiling = random_read_ceiling(torch, L)
 
@@ -286,14 +333,22 @@ def run_gpu(args, rank: int, world: int):
                     if isinstance(v, dict) else v) for k, v in summary.items()},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "bytes_per_op": BYTES_PER_OP[kinds[dom]]},
+                     "traffic": round(traffic) if traffic else None, "bytes_per_op": BYTES_PER_OP[kinds[dom]],
+                     "dram_gbs": round(traffic / (dom_ms * 1e-3) / 1e9, 1) if traffic else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, full-size capture"
+                     if traffic else "no capture for this kernel as built"},
         "random_read_ceiling": ceiling,
         "clocks": clk,
         "gpu_launches": len(calls) * world,
         "check": {"size_after_step": size_after, "expected": expected_size},
     }
-    out["other_ops"] = time_rehash_dump(t, torch)
-    if not args.no_e2e:
+    if in_kernel:
+        out["metric"] = "in-kernel function form: " + METRIC
+        out["config"]["form"] = "user kernel, one hcd::Table call per thread (examples/device_api.cu)"
+        out["config"]["launch"] = {"block": blk}
+    else:
+        out["other_ops"] = time_rehash_dump(t, torch)
+    if not args.no_e2e and not in_kernel:
         out["e2e"] = run_e2e(t, wl, fill, vals, hit, miss, er, stream)
     t.close()
     return out
@@ -753,7 +808,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     out = run_gpu(args, rank, world)
     if rank == 0:
-        if not args.no_cpu:
+        if not args.no_cpu and args.workload == "map_sweep":
             out["cpu_baseline"] = run_oracle_sample(args, args.cpu_sample_log2)
         print(json.dumps(out))
     if world > 1:

@@ -111,9 +111,8 @@ typedef struct hc_config {
  * selects the streaming form: a block stages its keys in shared memory and
  * each thread keeps 2 or 4 probes in flight, refilling as they finish (no
  * duplicate folding in this form).  Defaults:
- * lane_bytes = the bucket's key region (one thread per key), block 64,
- * folding off; keys_per_group 4 for inserts, 8 for erases, 4 for map lookups
- * and 1 for set lookups.  Results never depend on the
+ * lane_bytes = the bucket's key region (one thread per key),
+ * keys_per_group 4 (streaming), block 64, folding off.  Results never depend on the
  * shape. */
 typedef struct hc_launch {
     int32_t lane_bytes;       /* 32, 64 or 128, at most bucket_bytes     */
@@ -230,6 +229,49 @@ HC_API hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream);
  * returned.  Synchronises `stream`. */
 HC_API hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap,
               int64_t *n_out, void *stream);
+
+/* ---- in-kernel access: the function form inside the caller's kernels ----
+ * Section 4.1 lets single threads of a custom kernel call insert, find,
+ * contains and erase on a container passed to the kernel by value (a shallow
+ * copy, Section 3.7), with insertion as reliable as the range form.  The
+ * device functions live in include/hc_device.cuh; a kernel receives the
+ * hc_device_view below by value and wraps it in hcd::Table<kind>.
+ *
+ * Concurrency contract of the device functions (Section 4, "Guarantees":
+ * concurrency across all defined operations):
+ *   - Any mix of insert / find / contains / erase, from any threads of any
+ *     kernels, may run concurrently on one table.  The results for one key
+ *     are those of some serial order of that key's operations, and a key is
+ *     never stored twice.
+ *   - A map insert writes the value before its key becomes visible (under a
+ *     lock bit of the bucket it claims in), so a find that sees a key reads
+ *     the value stored with it.  Lookups take no lock (Section 4,
+ *     "Concurrency": lookups are non-blocking).
+ *   - In-kernel inserts claim EMPTY slots only, never tombstones: a
+ *     tombstone reused concurrently with another insert of the same key could
+ *     store the key twice.  Erased slots are reclaimed by hc_clear or
+ *     hc_rehash (or by range inserts), and an in-kernel insert returns
+ *     OVERFLOW when the key's probe sequence holds no EMPTY slot.
+ *   - Kernels that use the device functions and range calls on the same
+ *     table must be ordered (one stream, or events), like any two calls.
+ *
+ * hc_device_view fills *out for table t.  The view stays valid until the
+ * table is rehashed or destroyed.  For maps the first call allocates the
+ * lock bits (one per bucket, nb / 8 bytes rounded up to 4, zeroed on
+ * `stream` and freed with the table) and synchronises `stream`. */
+typedef struct hc_device_view {
+    void *buckets;          /* device: nb buckets of bucket_bytes bytes          */
+    void *header;           /* device: the table header (counters, side slots)   */
+    uint32_t *locks;        /* device: one lock bit per bucket (maps); NULL for sets */
+    uint64_t nb;            /* number of buckets                                 */
+    uint64_t seed;          /* hash seed                                         */
+    int32_t kind;           /* hc_kind                                           */
+    int32_t bucket_bytes;   /* 32, 64 or 128                                     */
+    int32_t hash_mode;      /* HC_HASH_*                                         */
+    int32_t pad_from;       /* slots of the last bucket at positions >= pad_from are padding */
+} hc_device_view;
+
+HC_API hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream);
 
 /* Device calibration: the time of one launch of n_reads reads of 32 bytes at
  * pseudo-random 32-byte-aligned offsets of d_buf (buf_bytes >= 64, 32-byte

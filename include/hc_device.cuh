@@ -1,0 +1,383 @@
+// hc_device.cuh -- in-kernel function form of the hash containers.
+//
+// Section 4.1 of "stdgpu: Efficient STL-like Data Structures on the GPU"
+// gives the containers two interfaces: range calls over whole arrays
+// (include/hc.h) and per-thread functions that custom kernels call on a
+// container passed to them by value (a shallow copy, Section 3.7): insert
+// returns where the key is stored and whether this call stored it, find
+// returns where it is stored or end, contains and erase report presence and
+// removal.  This header is that second interface.  A kernel receives the
+// hc_device_view of a table (hc_device_view_get) by value and wraps it:
+//
+//     __global__ void k(hc_device_view dv, const uint64_t *keys, int64_t n) {
+//         hcd::Table<HC_SET_U64> set(dv);
+//         const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+//         if (i < n) set.insert(keys[i]);
+//     }
+//
+// Every function is called by single threads, in divergent code if need
+// be; no warp-wide participation is required.  Layout, hashing and probing
+// are those of the library's own kernels (this header includes their device
+// core), so range calls and device functions see the same table.
+//
+// Concurrency (Section 4: modifications are thread-safe, lookups need no
+// lock, and every operation may run concurrently with every other; capacity
+// overflow is the only failure):
+//   insert   probes from the key's first bucket; stops at the key (EXISTS)
+//            or at the first bucket holding an EMPTY slot and claims the
+//            first EMPTY slot in a key-dependent order.  Only EMPTY slots
+//            are claimed, never tombstones.  Slots never become EMPTY again
+//            while kernels run, so every insert of one key reaches the same
+//            bucket and the same slot, and a key is stored at most once.
+//            Sets claim with one compare-and-swap of the key.  Maps take the
+//            bucket's lock bit first (one bit per bucket, an attempt that
+//            finds it held reads the bucket again: Section 5.2's locks
+//            without blocking), re-read the bucket, write the value, then
+//            the key, then release, so a reader that sees the key sees its
+//            value.  No EMPTY slot on the whole probe sequence: OVERFLOW.
+//   find     probes to the key or to a bucket holding EMPTY; takes no lock.
+//   erase    finds the key and swaps it for a tombstone.
+// Per key, the results of concurrent calls are those of some serial order
+// of them.  Counters (size) move with one atomic per group of threads that
+// finish an operation together.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hc.h"
+#include "../paper_1908_05936_gb300/csrc/hc_core.cuh"
+
+namespace hcd {
+
+enum : uint32_t { INSERTED = 0, EXISTS = 1, OVERFLOW = 2, ERASED = 3, NOT_FOUND = 4 };
+
+// The end position: returned by find for an absent key.
+constexpr long long END = -1;
+
+// Result of insert (the function form's pair of position and success):
+// `slot` is where the key is stored (END on overflow), `status` INSERTED when
+// this call stored it, EXISTS when it was there, OVERFLOW when it cannot be
+// stored.
+struct Inserted {
+    long long slot;
+    uint32_t status;
+};
+
+namespace detail {
+
+using hc::Header;
+using hc::View;
+
+// Bounds every wait and retry (lock bit held, compare-and-swap lost); a
+// correct table never reaches it.
+constexpr uint32_t kMaxRetries = hc::kMaxRestarts;
+
+__device__ __forceinline__ unsigned lane_id() {
+    unsigned l;
+    asm("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+
+// Counter updates of the threads that reach this point together: one atomic
+// per counter per group.
+__device__ __forceinline__ void count(Header *h, uint32_t ins, uint32_t del, uint32_t used) {
+    const unsigned m = __activemask();
+    const uint32_t a = __reduce_add_sync(m, ins);
+    const uint32_t d = __reduce_add_sync(m, del);
+    const uint32_t u = __reduce_add_sync(m, used);
+    if (lane_id() == (unsigned)(__ffs(m) - 1)) {
+        const long long net = (long long)a - (long long)d;
+        if (net) atomicAdd(&h->live, (unsigned long long)net);
+        if (u) atomicAdd(&h->used, (unsigned long long)u);
+    }
+}
+
+__device__ __forceinline__ bool try_lock(uint32_t *words, unsigned long long i) {
+    const uint32_t bit = 1u << (i & 31);
+    if (atomicOr(&words[i >> 5], bit) & bit) return false;
+    __threadfence();                                  // acquire: the bucket is read after the bit is held
+    return true;
+}
+
+__device__ __forceinline__ void unlock(uint32_t *words, unsigned long long i) {
+    __threadfence();                                  // release: the slot's writes before the bit
+    atomicAnd(&words[i >> 5], ~(1u << (i & 31)));
+}
+
+// First set bit of `mask` at or after position `rot`, wrapping around.
+template <int SPB>
+__device__ __forceinline__ int first_from(uint32_t mask, int rot) {
+    constexpr uint32_t ALL = SPB >= 32 ? 0xFFFFFFFFu : ((1u << SPB) - 1u);
+    const uint32_t hi = mask & (ALL & ~((1u << rot) - 1u));
+    return __ffs(hi ? hi : mask) - 1;
+}
+
+template <int KIND, int BB>
+__device__ __forceinline__ void scan(const View &v, unsigned long long b, typename hc::Traits<KIND>::Key k,
+                                     uint32_t &match, uint32_t &empty) {
+    using S = hc::Slots<KIND, BB>;
+    hc::LaneWords<S::KRB> lw;
+    lw.load(v.buckets + b * BB);
+    match = 0;
+    empty = 0;
+#pragma unroll
+    for (int q = 0; q < S::SPB; ++q) {
+        const auto ks = hc::slot_key<KIND, S::KRB>(lw, q);
+        match |= (uint32_t)(ks == k) << q;
+        empty |= (uint32_t)(ks == hc::Traits<KIND>::EMPTY) << q;
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_key(unsigned char *slot, typename hc::Traits<KIND>::Key k) {
+    if constexpr (sizeof(k) == 4) atomicExch(reinterpret_cast<unsigned int *>(slot), (unsigned int)k);
+    else atomicExch(reinterpret_cast<unsigned long long *>(slot), (unsigned long long)k);
+}
+
+// Keys equal to the EMPTY / TOMBSTONE bit patterns live in the header's side
+// slots; their positions are nb * SPB + side.
+template <int KIND>
+__device__ Inserted insert_side(const View &v, int side, unsigned long long val, long long pos) {
+    using T = hc::Traits<KIND>;
+    Header *h = v.hdr;
+    Inserted r{pos, EXISTS};
+    uint32_t ins = 0;
+    if constexpr (T::MAP) {
+        uint32_t tries = 0;
+        const uint32_t bit = 1u << side;
+        while (true) {
+            if (*((volatile unsigned int *)&h->side_present[side])) break;       // present: EXISTS
+            if (!(atomicOr(&h->side_lock, bit) & bit)) {
+                __threadfence();
+                if (!*((volatile unsigned int *)&h->side_present[side])) {
+                    *((volatile unsigned long long *)&h->side_val[side]) = val;
+                    __threadfence();
+                    atomicExch(&h->side_present[side], 1u);
+                    r.status = INSERTED;
+                    ins = 1;
+                }
+                __threadfence();
+                atomicAnd(&h->side_lock, ~bit);
+                break;
+            }
+            if (++tries > kMaxRetries) {
+                atomicOr(&h->err, hc::ERR_PROBE_BOUND);
+                r = Inserted{END, OVERFLOW};
+                break;
+            }
+        }
+    } else {
+        if (atomicCAS(&h->side_present[side], 0u, 1u) == 0u) {
+            r.status = INSERTED;
+            ins = 1;
+        }
+    }
+    count(h, ins, 0, 0);
+    return r;
+}
+
+template <int KIND, int BB>
+__device__ Inserted insert(const View &v, uint32_t *locks, typename hc::Traits<KIND>::Key k,
+                           unsigned long long val) {
+    using T = hc::Traits<KIND>;
+    using S = hc::Slots<KIND, BB>;
+    constexpr int SPB = S::SPB;
+    const int side = hc::side_index<KIND>(k);
+    if (side >= 0) return insert_side<KIND>(v, side, val, (long long)(v.nb * SPB) + side);
+    const int rot = hc::slot_rotation<SPB>((unsigned long long)k);
+    unsigned long long b = hc::first_bucket(v, (unsigned long long)k);
+    Inserted r{END, OVERFLOW};
+    uint32_t ins = 0, retries = 0;
+    bool bound = false;
+    for (unsigned long long p = 0; p < v.nb;) {
+        uint32_t lm, le;
+        scan<KIND, BB>(v, b, k, lm, le);
+        if (lm) {
+            r = Inserted{(long long)(b * SPB) + (__ffs(lm) - 1), EXISTS};
+            break;
+        }
+        if (!le) {
+            b = hc::next_bucket(v, b);
+            ++p;
+            continue;
+        }
+        if constexpr (T::MAP) {
+            if (!try_lock(locks, b)) {                 // held: read the bucket again
+                if (++retries > kMaxRetries) { bound = true; break; }
+                continue;
+            }
+            scan<KIND, BB>(v, b, k, lm, le);           // under the lock
+            if (lm || !le) {
+                unlock(locks, b);
+                if (lm) {
+                    r = Inserted{(long long)(b * SPB) + (__ffs(lm) - 1), EXISTS};
+                    break;
+                }
+                b = hc::next_bucket(v, b);
+                ++p;
+                continue;
+            }
+            const int q = first_from<SPB>(le, rot);
+            hc::store_val<KIND, BB>(v, b, q, val);
+            __threadfence();                           // the value before the key
+            store_key<KIND>(S::key(v, b, q), k);
+            unlock(locks, b);
+            r = Inserted{(long long)(b * SPB) + q, INSERTED};
+            ins = 1;
+            break;
+        } else {
+            const int q = first_from<SPB>(le, rot);
+            const auto old = hc::cas_key<KIND>(S::key(v, b, q), T::EMPTY, k);
+            if (old == T::EMPTY) {
+                r = Inserted{(long long)(b * SPB) + q, INSERTED};
+                ins = 1;
+                break;
+            }
+            if (old == k) {
+                r = Inserted{(long long)(b * SPB) + q, EXISTS};
+                break;
+            }
+            // another key took the slot: the same bucket is read again (an
+            // equal key can only have gone to this bucket or a later one)
+            if (++retries > kMaxRetries) { bound = true; break; }
+        }
+    }
+    if (r.status == OVERFLOW) atomicOr(&v.hdr->err, bound ? (hc::ERR_PROBE_BOUND | hc::ERR_OVERFLOW) : hc::ERR_OVERFLOW);
+    count(v.hdr, ins, 0, ins);
+    return r;
+}
+
+template <int KIND, int BB>
+__device__ long long find(const View &v, typename hc::Traits<KIND>::Key k) {
+    using S = hc::Slots<KIND, BB>;
+    constexpr int SPB = S::SPB;
+    const int side = hc::side_index<KIND>(k);
+    if (side >= 0)
+        return *((volatile unsigned int *)&v.hdr->side_present[side]) ? (long long)(v.nb * SPB) + side : END;
+    unsigned long long b = hc::first_bucket(v, (unsigned long long)k);
+    for (unsigned long long p = 0; p < v.nb; ++p) {
+        uint32_t lm, le;
+        scan<KIND, BB>(v, b, k, lm, le);
+        if (lm) return (long long)(b * SPB) + (__ffs(lm) - 1);
+        if (le) return END;
+        b = hc::next_bucket(v, b);
+    }
+    return END;
+}
+
+template <int KIND, int BB>
+__device__ uint32_t erase(const View &v, typename hc::Traits<KIND>::Key k) {
+    using T = hc::Traits<KIND>;
+    using S = hc::Slots<KIND, BB>;
+    constexpr int SPB = S::SPB;
+    uint32_t del = 0;
+    const int side = hc::side_index<KIND>(k);
+    if (side >= 0) {
+        del = atomicCAS(&v.hdr->side_present[side], 1u, 0u) == 1u;
+    } else {
+        const long long pos = find<KIND, BB>(v, k);
+        if (pos != END) {
+            const unsigned long long b = (unsigned long long)pos / SPB;
+            const int q = (int)((unsigned long long)pos % SPB);
+            // a failed swap means a concurrent erase of the same key won
+            del = hc::cas_key<KIND>(S::key(v, b, q), k, T::TOMB) == k;
+        }
+    }
+    count(v.hdr, 0, del, 0);
+    return del ? ERASED : NOT_FOUND;
+}
+
+template <int KIND, int BB>
+__device__ typename hc::Traits<KIND>::Val value_at(const View &v, long long pos) {
+    using T = hc::Traits<KIND>;
+    using S = hc::Slots<KIND, BB>;
+    __threadfence();                                   // after the load that found the key
+    const unsigned long long phys = v.nb * S::SPB;
+    if ((unsigned long long)pos >= phys)
+        return (typename T::Val) * ((volatile unsigned long long *)&v.hdr->side_val[pos - (long long)phys]);
+    return (typename T::Val)hc::load_val<KIND, BB>(v, (unsigned long long)pos / S::SPB, (int)(pos % S::SPB));
+}
+
+template <int KIND, int BB>
+__device__ typename hc::Traits<KIND>::Key key_at(const View &v, long long pos) {
+    using T = hc::Traits<KIND>;
+    using S = hc::Slots<KIND, BB>;
+    const unsigned long long phys = v.nb * S::SPB;
+    if ((unsigned long long)pos >= phys) return pos - (long long)phys == 0 ? T::EMPTY : T::TOMB;
+    const unsigned char *p = S::key(v, (unsigned long long)pos / S::SPB, (int)(pos % S::SPB));
+    return *reinterpret_cast<const volatile typename T::Key *>(p);
+}
+
+}  // namespace detail
+
+// A table of kind KIND (HC_SET_U32, HC_SET_U64, HC_MAP_I64_I32,
+// HC_MAP_U64_U64) seen from a kernel.  Keys and values are the bit patterns
+// of the kind's types (int64 keys and int32 values as uint64 / uint32).
+template <int KIND>
+class Table {
+public:
+    using Key = typename hc::Traits<KIND>::Key;
+    using Val = typename hc::Traits<KIND>::Val;
+    static constexpr bool is_map = hc::Traits<KIND>::MAP;
+
+    __host__ __device__ explicit Table(const hc_device_view &d) : locks_(d.locks), bb_(d.bucket_bytes) {
+        v_.buckets = static_cast<unsigned char *>(d.buckets);
+        v_.hdr = static_cast<hc::Header *>(d.header);
+        v_.nb = d.nb;
+        v_.seed = d.seed;
+        v_.hash_mode = d.hash_mode;
+        v_.pad_from = d.pad_from;
+        v_.rotate = 1;
+        v_.reserved = 0;
+    }
+
+    // Stores `key` (with `value` for maps) unless it is present.
+    __device__ Inserted insert(Key key, Val value = Val()) const {
+        switch (bb_) {
+            case 32: return detail::insert<KIND, 32>(v_, locks_, key, (unsigned long long)value);
+            case 64: return detail::insert<KIND, 64>(v_, locks_, key, (unsigned long long)value);
+            default: return detail::insert<KIND, 128>(v_, locks_, key, (unsigned long long)value);
+        }
+    }
+    // Position of `key`, or END.
+    __device__ long long find(Key key) const {
+        switch (bb_) {
+            case 32: return detail::find<KIND, 32>(v_, key);
+            case 64: return detail::find<KIND, 64>(v_, key);
+            default: return detail::find<KIND, 128>(v_, key);
+        }
+    }
+    __device__ bool contains(Key key) const { return find(key) != END; }
+    // ERASED when this call removed `key`, NOT_FOUND otherwise.
+    __device__ uint32_t erase(Key key) const {
+        switch (bb_) {
+            case 32: return detail::erase<KIND, 32>(v_, key);
+            case 64: return detail::erase<KIND, 64>(v_, key);
+            default: return detail::erase<KIND, 128>(v_, key);
+        }
+    }
+    // The value stored at a position that find or insert returned (maps).
+    __device__ Val value(long long pos) const {
+        switch (bb_) {
+            case 32: return detail::value_at<KIND, 32>(v_, pos);
+            case 64: return detail::value_at<KIND, 64>(v_, pos);
+            default: return detail::value_at<KIND, 128>(v_, pos);
+        }
+    }
+    // The key stored at a position that find or insert returned.
+    __device__ Key key(long long pos) const {
+        switch (bb_) {
+            case 32: return detail::key_at<KIND, 32>(v_, pos);
+            case 64: return detail::key_at<KIND, 64>(v_, pos);
+            default: return detail::key_at<KIND, 128>(v_, pos);
+        }
+    }
+
+private:
+    hc::View v_;
+    uint32_t *locks_;
+    int bb_;
+};
+
+}  // namespace hcd

@@ -29,7 +29,7 @@ EXPORTS = [
     "hc_get_launch", "hc_insert", "hc_insert_if_absent", "hc_find", "hc_erase", "hc_insert_host", "hc_find_host", "hc_erase_host",
     "hc_size", "hc_stats", "hc_status", "hc_clear", "hc_rehash", "hc_dump", "hc_batch_create",
     "hc_batch_launch", "hc_batch_destroy", "hc_batch_run_noalloc", "hc_measure_random_reads",
-    "hc_batch_scratch_bytes", "hc_batch_run",
+    "hc_batch_scratch_bytes", "hc_batch_run", "hc_device_view_get",
 ]
 
 
@@ -63,6 +63,13 @@ class BatchItem(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("lane_bytes", ctypes.c_int32), ("keys_per_group", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class DeviceView(ctypes.Structure):
+    """hc_device_view: a table as the in-kernel functions see it."""
+    _fields_ = [("buckets", ctypes.c_void_p), ("header", ctypes.c_void_p), ("locks", ctypes.c_void_p),
+                ("nb", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("kind", ctypes.c_int32),
+                ("bucket_bytes", ctypes.c_int32), ("hash_mode", ctypes.c_int32), ("pad_from", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -100,6 +107,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_measure_random_reads": (i32, [vp, i64, i64, i32, P(ctypes.c_float), vp]),
         "hc_batch_scratch_bytes": (i64, [i64]),
         "hc_batch_run": (i32, [P(BatchItem), i64, P(BatchConfig), vp, i64, vp]),
+        "hc_device_view_get": (i32, [vp, P(DeviceView), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

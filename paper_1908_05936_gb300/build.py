@@ -1,5 +1,7 @@
 """Build libhc.so in-tree: every CUDA translation unit compiled for sm_103a in
-parallel with nvcc, then linked into one shared library.
+parallel with nvcc, then linked into one shared library.  The user kernels of
+examples/ (written against the public headers only) become
+libhc_examples.so.
 
     python -m paper_1908_05936_gb300.build
 """
@@ -15,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhc.so")
+EXAMPLES_SRC = os.path.join(HERE, "examples", "device_api.cu")
+EXAMPLES_LIB = os.path.join(HERE, "libhc_examples.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,11 +40,18 @@ def _deps() -> list[str]:
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "hc.h")]
 
 
+def _example_deps() -> list[str]:
+    inc = os.path.join(ROOT, "include")
+    return [EXAMPLES_SRC, os.path.join(inc, "hc.h"), os.path.join(inc, "hc_device.cuh"),
+            os.path.join(CSRC, "hc_core.cuh")]
+
+
 def stale(lib: str = LIB) -> bool:
     if not os.path.exists(lib):
         return True
     t = os.path.getmtime(lib)
-    return any(os.path.getmtime(d) > t for d in _deps())
+    deps = _example_deps() if lib == EXAMPLES_LIB else _deps()
+    return any(os.path.getmtime(d) > t for d in deps)
 
 
 def _compile(src: str, extra: list[str]) -> str:
@@ -50,6 +61,21 @@ def _compile(src: str, extra: list[str]) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
     return obj
+
+
+def build_examples(force: bool = False, verbose: bool = False) -> str:
+    """Compile libhc_examples.so (the device-API user kernels); returns its path."""
+    if not force and not stale(EXAMPLES_LIB):
+        return EXAMPLES_LIB
+    tmp = EXAMPLES_LIB + ".tmp"
+    cmd = [nvcc(), *ARCH, *FLAGS, "-shared", EXAMPLES_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {EXAMPLES_SRC}:\n{r.stderr}")
+    os.replace(tmp, EXAMPLES_LIB)
+    if verbose:
+        print(f"built {EXAMPLES_LIB}")
+    return EXAMPLES_LIB
 
 
 def build(force: bool = False, extra: list[str] | None = None, verbose: bool = False) -> str:
@@ -73,3 +99,4 @@ def build(force: bool = False, extra: list[str] | None = None, verbose: bool = F
 
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True)
+    build_examples(force="--force" in sys.argv, verbose=True)

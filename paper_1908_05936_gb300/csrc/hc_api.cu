@@ -303,14 +303,10 @@ hc_rc hc_create(hc_table **out, int32_t kind, int64_t slots, const hc_config *cf
         return fail(HC_ERR_OOM, "cudaMalloc of %lld bytes failed: %s", (long long)g.bytes, cudaGetErrorString(e));
     }
     t->view = make_view(t->d_mem, g, seed, hm);
-    // one thread per key reading the bucket's keys, 64-thread blocks: the
-    // best shapes of the sweeps on GB300 for uniform keys.  Inserts stream 4
-    // keys per thread (2 in flight), erases 8 (4 in flight), map lookups 4;
-    // set lookups run one key per thread in lock step.
-    for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{key_region_bytes(kind, bb), 1, 64, 0, 0};
-    t->shape[hc::OP_INSERT].keys_per_group = 4;
-    t->shape[hc::OP_ERASE].keys_per_group = 8;
-    if (is_map(kind)) t->shape[hc::OP_FIND].keys_per_group = 4;
+    // the streaming kernels, one thread per key reading the bucket's keys,
+    // 4 keys per thread with 2 probes in flight, 64-thread blocks: the best
+    // shape of the sweeps on GB300 for uniform keys, for every kind and op.
+    for (int op = 0; op < 3; ++op) t->shape[op] = hc::LaunchShape{key_region_bytes(kind, bb), 4, 64, 0, 0};
     e = dispatch_clear(t, t->view, t->phys, t->capacity, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         cudaFree(t->d_mem);
@@ -327,6 +323,7 @@ hc_rc hc_destroy(hc_table *t) {
     if (rc != HC_OK) return rc;
     t->magic = 0;
     cudaError_t e = cudaFree(t->d_mem);   // cudaFree waits for work queued on the device
+    if (t->locks) cudaFree(t->locks);
     if (t->stage_mem) {
         cudaFree(t->stage_mem);
         for (int i = 0; i < 2; ++i) {
@@ -494,6 +491,10 @@ hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
         return cuda_fail(e, "rehashing");
     }
     cudaFree(t->d_mem);
+    if (t->locks) {                       // sized for the old bucket count; the next view allocates anew
+        cudaFree(t->locks);
+        t->locks = nullptr;
+    }
     t->d_mem = mem;
     t->view = nv;
     t->capacity = new_slots;
@@ -532,6 +533,41 @@ hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap, int6
     if ((long long)h.dump_count > cap)
         return fail(HC_ERR_ARG, "%lld stored keys do not fit the %lld output entries", (long long)h.dump_count,
                     (long long)cap);
+    return HC_OK;
+}
+
+
+hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream) {
+    hc_rc rc = check_table(t);
+    if (rc != HC_OK) return rc;
+    if (!out) return fail(HC_ERR_ARG, "out is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (is_map(t->kind) && !t->locks) {
+        const size_t words = (size_t)((t->view.nb + 31) / 32);
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, words * sizeof(uint32_t));
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(HC_ERR_OOM, "cudaMalloc of %lld lock bytes failed: %s", (long long)(words * 4),
+                        cudaGetErrorString(e));
+        }
+        e = cudaMemsetAsync(p, 0, words * sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return cuda_fail(e, "zeroing the lock bits");
+        }
+        t->locks = static_cast<uint32_t *>(p);
+    }
+    out->buckets = t->view.buckets;
+    out->header = t->view.hdr;
+    out->locks = t->locks;
+    out->nb = t->view.nb;
+    out->seed = t->view.seed;
+    out->kind = t->kind;
+    out->bucket_bytes = t->bucket_bytes;
+    out->hash_mode = t->view.hash_mode;
+    out->pad_from = t->view.pad_from;
     return HC_OK;
 }
 

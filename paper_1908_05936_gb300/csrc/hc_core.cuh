@@ -65,7 +65,7 @@ struct alignas(256) Header {
     unsigned long long used;             // slots that are not EMPTY (keys + tombstones), padding excluded
     unsigned int err;                    // sticky ERR_* bits
     unsigned int side_present[2];        // [0]: all-ones key, [1]: all-ones-minus-one key
-    unsigned int pad0;
+    unsigned int side_lock;              // bits 0/1: side slot held by an in-kernel map insert
     unsigned long long side_val[2];
     unsigned long long dump_count;       // output cursor of the dump kernel
     unsigned long long reinserted;       // counter of the rehash kernel

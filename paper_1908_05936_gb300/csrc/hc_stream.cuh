@@ -8,10 +8,23 @@
 
 #include "hc_core.cuh"
 
+// Minimum resident 256-thread blocks per SM requested from the compiler
+// (__launch_bounds__), i.e. a register cap of 65536 / (256 * MINB) per
+// thread; build options.
+#ifndef HC_STREAM_FIND_MINB
+#define HC_STREAM_FIND_MINB 1
+#endif
+#ifndef HC_STREAM_INSERT_MINB
+#define HC_STREAM_INSERT_MINB 1
+#endif
+#ifndef HC_STREAM_ERASE_MINB
+#define HC_STREAM_ERASE_MINB 1
+#endif
+
 namespace hc {
 
 template <int KIND, int BB, int KPT, int S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, HC_STREAM_FIND_MINB)
 k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *found,
               typename Traits<KIND>::Val *vals_out) {
     using T = Traits<KIND>;
@@ -110,7 +123,7 @@ k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8
 // stores; counters leave with one atomic per warp.  Equal keys inside a warp
 // are not folded here (folding is a lock-step option).
 template <int KIND, int BB, int KPT, int S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, HC_STREAM_INSERT_MINB)
 k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
                 uint8_t *status, const uint8_t *skip) {
     using T = Traits<KIND>;
@@ -271,7 +284,7 @@ k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename T
 // same call erased the slot first: that key reports ERASED, this one
 // NOT_FOUND, as in the lock-step form.
 template <int KIND, int BB, int KPT, int S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, HC_STREAM_ERASE_MINB)
 k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status) {
     using T = Traits<KIND>;
     using Key = typename T::Key;

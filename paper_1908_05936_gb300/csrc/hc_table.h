@@ -21,6 +21,7 @@ struct hc_table {
     void *d_mem;          // header followed by the slots
     hc::View view;
     hc::LaunchShape shape[3];
+    uint32_t *locks = nullptr;   // lock bits of the in-kernel map insert (one per bucket), on first use
     // staging for the host-buffer calls (allocated on first use)
     void *stage_mem = nullptr;
     cudaStream_t copy_stream = nullptr;

@@ -210,6 +210,12 @@ class Table:
         return status
 
     # ------------------------------------------------------- whole table --
+    def device_view(self, stream=None) -> L.DeviceView:
+        """The hc_device_view that kernels using include/hc_device.cuh take."""
+        dv = L.DeviceView()
+        L.check(self.lib.hc_device_view_get(self.h, ctypes.byref(dv), _stream_handle(stream)))
+        return dv
+
     def size(self, stream=None) -> int:
         v = ctypes.c_int64()
         L.check(self.lib.hc_size(self.h, ctypes.byref(v), _stream_handle(stream)))

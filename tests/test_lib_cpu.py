@@ -66,3 +66,24 @@ def test_table_bytes(lib):
     assert lib.hc_table_bytes(L.SET_U64, 17, ctypes.byref(cfg), ctypes.byref(b)) == L.OK
     assert b.value == 256 + 256           # two 128-byte buckets
     assert lib.hc_table_bytes(L.SET_U64, 0, None, ctypes.byref(b)) == L.ERR_ARG
+
+
+def test_examples_library_exports_and_argument_errors(lib):
+    """libhc_examples.so (user kernels on include/hc_device.cuh) builds against
+    the public headers alone, loads, and rejects bad arguments before any
+    launch; hc_device_view_get rejects a NULL table."""
+    from paper_1908_05936_gb300 import _lib as L
+    from paper_1908_05936_gb300 import build
+    from paper_1908_05936_gb300 import device_api as D
+    build.build_examples()
+    ex = D.load_examples()
+    for name in ("hcx_apply", "hcx_update_set"):
+        assert hasattr(ex, name), name
+    dv = L.DeviceView()
+    assert lib.hc_device_view_get(None, ctypes.byref(dv), None) == L.ERR_ARG
+    assert ex.hcx_apply(None, None, 0, None, None, 1, None, None, None, 128, None) == L.ERR_ARG
+    dv.kind = 9
+    assert ex.hcx_apply(ctypes.byref(dv), None, 0, None, None, 0, None, None, None, 128, None) == L.OK
+    assert ex.hcx_apply(ctypes.byref(dv), None, 3, None, None, 1, None, None, None, 128, None) == L.ERR_ARG
+    assert ex.hcx_apply(ctypes.byref(dv), None, 0, None, None, 1, None, None, None, 100, None) == L.ERR_ARG
+    assert ex.hcx_update_set(ctypes.byref(dv), ctypes.byref(dv), None, 1, None) == L.ERR_ARG
