@@ -374,10 +374,96 @@ public:
         }
     }
 
+    // Number of positions: every slot of the table, then the two side slots.
+    __device__ long long positions() const { return (long long)(v_.nb * (unsigned long long)spb()) + 2; }
+
+    // Whether position `pos` holds a stored key; if so, *k (and *val for maps,
+    // when not NULL) receive it.  Meant for ranges over the stored entries while
+    // no insert or erase runs on the table.
+    __device__ bool entry(long long pos, Key *k, Val *val = nullptr) const {
+        using T = hc::Traits<KIND>;
+        const unsigned long long phys = v_.nb * (unsigned long long)spb();
+        if ((unsigned long long)pos >= phys) {
+            const int side = (int)((unsigned long long)pos - phys);
+            if (!*((volatile unsigned int *)&v_.hdr->side_present[side])) return false;
+            *k = side == 0 ? T::EMPTY : T::TOMB;
+            if constexpr (T::MAP) {
+                if (val) *val = (Val) * ((volatile unsigned long long *)&v_.hdr->side_val[side]);
+            }
+            return true;
+        }
+        const Key key = this->key(pos);
+        if (key == T::EMPTY || key == T::TOMB) return false;
+        *k = key;
+        if constexpr (T::MAP) {
+            if (val) *val = value_plain(pos);
+        }
+        return true;
+    }
+
 private:
+    __device__ int spb() const {
+        switch (bb_) {
+            case 32: return hc::Slots<KIND, 32>::SPB;
+            case 64: return hc::Slots<KIND, 64>::SPB;
+            default: return hc::Slots<KIND, 128>::SPB;
+        }
+    }
+    __device__ Val value_plain(long long pos) const {
+        switch (bb_) {
+            case 32: return (Val)hc::load_val<KIND, 32>(v_, pos / hc::Slots<KIND, 32>::SPB, (int)(pos % hc::Slots<KIND, 32>::SPB));
+            case 64: return (Val)hc::load_val<KIND, 64>(v_, pos / hc::Slots<KIND, 64>::SPB, (int)(pos % hc::Slots<KIND, 64>::SPB));
+            default:
+                return (Val)hc::load_val<KIND, 128>(v_, pos / hc::Slots<KIND, 128>::SPB,
+                                                    (int)(pos % hc::Slots<KIND, 128>::SPB));
+        }
+    }
+
     hc::View v_;
     uint32_t *locks_;
     int bb_;
 };
+
+// Selection over the stored entries (Section 3.6's block selection: a range
+// over a container, copied with a predicate through a back inserter into a
+// vector).  Appends every stored (key, value) with
+// pred(key, value) true to keys_out / vals_out (vals_out may be NULL; sets
+// pass NULL) through *size, the output vector's element count: an entry's
+// position is the count before it, entries at positions >= cap are counted
+// but not written.  Every thread of the calling grid calls it with the same
+// arguments; blocks must be one-dimensional whole warps.  Each warp walks the
+// positions in steps of 32 and appends its matches with one atomic add.  No
+// insert or erase may run on the table meanwhile.
+template <int KIND, class Pred>
+__device__ void copy_if(const Table<KIND> &t, Pred pred, typename Table<KIND>::Key *keys_out,
+                        typename Table<KIND>::Val *vals_out, unsigned long long cap, unsigned long long *size) {
+    using Key = typename Table<KIND>::Key;
+    using Val = typename Table<KIND>::Val;
+    const unsigned lane = detail::lane_id();
+    const long long total = t.positions();
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    const long long w = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    for (long long base = w * 32; base < total; base += warps * 32) {
+        const long long pos = base + lane;
+        Key k{};
+        Val v{};
+        bool hit = false;
+        if (pos < total && t.entry(pos, &k, Table<KIND>::is_map ? &v : nullptr)) hit = pred(k, v);
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (!m) continue;
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(size, (unsigned long long)__popc(m));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (hit) {
+            const unsigned long long at = first + __popc(m & ((1u << lane) - 1u));
+            if (at < cap) {
+                keys_out[at] = k;
+                if constexpr (Table<KIND>::is_map) {
+                    if (vals_out) vals_out[at] = v;
+                }
+            }
+        }
+    }
+}
 
 }  // namespace hcd
