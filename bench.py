@@ -374,9 +374,32 @@ def time_rehash_dump(t, torch):
     size_s = time.perf_counter() - t0
     assert len(k) == live == st1["live"] == st0["live"]
     del k, v
+    # selection of about 1/16 of the entries (keys below 2^60), timed with
+    # CUDA events: one pass over every slot's key, values of the matches
+    from paper_1908_05936_gb300 import _lib as L
+    ko = torch.empty(live // 8, dtype=torch.int64, device="cuda")
+    vo = torch.empty(live // 8, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    t.select(L.PRED_KEY_RANGE, 0, 2**60 - 1, keys_out=ko, vals_out=vo, count=cnt)
+    ms = []
+    for _ in range(5):
+        cnt.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        t.select(L.PRED_KEY_RANGE, 0, 2**60 - 1, keys_out=ko, vals_out=vo, count=cnt)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    sel = int(cnt.item())
+    sel_ms = float(np.median(ms))
+    key_bytes = st1["capacity"] * 8          # every slot's key is read once
+    del ko, vo
     return {"rehash": {"ms": round(rehash_s * 1e3, 2), "live": st0["live"], "used_before": st0["used"],
                        "used_after": st1["used"], "mkeys_per_s": round(st0["live"] / rehash_s / 1e6, 1)},
             "dump": {"ms": round(dump_s * 1e3, 2), "mkeys_per_s": round(live / dump_s / 1e6, 1)},
+            "select": {"ms": round(sel_ms, 3), "selected": sel, "slots_per_s_g": round(st1["capacity"] / sel_ms / 1e6, 1),
+                       "key_gbs": round((key_bytes + sel * 32) / (sel_ms * 1e-3) / 1e9, 1)},
             "size": {"us": round(size_s * 1e6, 1)}}
 
 

@@ -230,6 +230,46 @@ HC_API hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream);
 HC_API hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap,
               int64_t *n_out, void *stream);
 
+/* ---- selection over the stored entries ----------------------------------
+ * Section 3.6 selects, for example, the voxel blocks a camera sees: a range
+ * over a container's stored entries, copied with a predicate through a back
+ * inserter into a vector.  hc_select does this with the predicates below;
+ * kernels of the caller's own can use any predicate with hcd::copy_if of
+ * include/hc_device.cuh. */
+typedef enum hc_pred_kind {
+    HC_PRED_ALL = 0,          /* every stored entry                                  */
+    HC_PRED_KEY_RANGE = 1,    /* lo <= key <= hi, compared in the key type: uint32
+                                 (HC_SET_U32, lo/hi taken mod 2^32), uint64, or int64
+                                 (HC_MAP_I64_I32)                                     */
+    HC_PRED_VALUE_RANGE = 2,  /* maps: lo <= value <= hi in the value type, uint64 or
+                                 int32 (lo/hi as int64)                               */
+    HC_PRED_KEY_MASK = 3,     /* (key & lo) == hi on the key's bits                   */
+    HC_PRED_BLOCK_BOX = 4     /* 64-bit keys packing three signed 21-bit block
+                                 coordinates x | y << 21 | z << 42 (Section 4.1's
+                                 voxel blocks): box[0] <= x <= box[1],
+                                 box[2] <= y <= box[3], box[4] <= z <= box[5]        */
+} hc_pred_kind;
+
+typedef struct hc_predicate {
+    int32_t kind;     /* hc_pred_kind                                          */
+    int32_t negate;   /* 0, or 1 to select the entries the predicate rejects   */
+    int64_t lo, hi;   /* bounds, or mask and match                             */
+    int32_t box[6];   /* HC_PRED_BLOCK_BOX bounds, inclusive                   */
+} hc_predicate;
+
+/* Append every stored (key, value) that satisfies *pred to device arrays of
+ * `cap` entries, d_keys_out and (maps, may be NULL) d_vals_out, through
+ * *d_count: a DEVICE int64 holding the output vector's current size.  Each
+ * selected entry goes to the position *d_count had before it and increments
+ * it, so several calls append one after another; entries at positions >= cap
+ * are counted but not written (the caller sees *d_count > cap).  Order of the
+ * appended entries is unspecified.  Asynchronous on `stream`; no insert or
+ * erase may run on the table meanwhile.  HC_ERR_ARG for a NULL d_count or
+ * pred, an unknown predicate kind, HC_PRED_VALUE_RANGE on a set, or
+ * HC_PRED_BLOCK_BOX on HC_SET_U32. */
+HC_API hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, void *d_vals_out, int64_t cap,
+                       int64_t *d_count, void *stream);
+
 /* ---- in-kernel access: the function form inside the caller's kernels ----
  * Section 4.1 lets single threads of a custom kernel call insert, find,
  * contains and erase on a container passed to the kernel by value (a shallow

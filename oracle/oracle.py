@@ -27,6 +27,8 @@ LIB = os.path.join(BUILD, "liboracle.so")
 SET_U32, SET_U64, MAP_I64_I32, MAP_U64_U64 = 0, 1, 2, 3
 INSERTED, EXISTS, OVERFLOW, ERASED, NOT_FOUND = 0, 1, 2, 3, 4
 
+PRED_ALL, PRED_KEY_RANGE, PRED_VALUE_RANGE, PRED_KEY_MASK, PRED_BLOCK_BOX = 0, 1, 2, 3, 4
+
 KEY_DTYPE = {SET_U32: np.uint32, SET_U64: np.uint64, MAP_I64_I32: np.int64, MAP_U64_U64: np.uint64}
 VAL_DTYPE = {MAP_I64_I32: np.int32, MAP_U64_U64: np.uint64}
 
@@ -165,3 +167,48 @@ class OracleTable:
         self.lib.o_dump(self.h, _ptr(k), _ptr(v), n)
         order = np.argsort(k.view(np.uint32 if self.kdt == np.uint32 else np.uint64), kind="stable")
         return k[order], (v[order] if v is not None else None)
+
+    def select(self, pred_kind: int, lo: int = 0, hi: int = 0, box=(0, 0, 0, 0, 0, 0), negate: bool = False):
+        """Stored (keys, values) that satisfy the predicate (Section 3.6: a
+        range over the stored entries copied with a predicate), sorted by key
+        bit pattern."""
+        k, v = self.dump()
+        keep = [selected(self.kind, pred_kind, lo, hi, box, negate, int(k[i]), None if v is None else int(v[i]))
+                for i in range(len(k))]
+        keep = np.array(keep, dtype=bool)
+        return k[keep], (v[keep] if v is not None else None)
+
+
+def _block_coord(key_bits: int, field: int) -> int:
+    """Signed 21-bit field `field` (0 = x, 1 = y, 2 = z) of a packed block key."""
+    c = (key_bits >> (21 * field)) & 0x1FFFFF
+    return c - (1 << 21) if c >= (1 << 20) else c
+
+
+def selected(kind: int, pred_kind: int, lo: int, hi: int, box, negate: bool, key: int, val) -> bool:
+    """One entry against one predicate.  `key` and `val` are the entry's
+    values in the container's own types (int64 keys and int32 values signed,
+    the others unsigned); bounds are compared in those types."""
+    kbits = key & 0xFFFFFFFFFFFFFFFF
+    if pred_kind == PRED_ALL:
+        r = True
+    elif pred_kind == PRED_KEY_RANGE:
+        if kind == MAP_I64_I32:
+            r = lo <= key <= hi
+        elif kind == SET_U32:
+            r = (lo & 0xFFFFFFFF) <= key <= (hi & 0xFFFFFFFF)
+        else:
+            r = (lo & 0xFFFFFFFFFFFFFFFF) <= key <= (hi & 0xFFFFFFFFFFFFFFFF)
+    elif pred_kind == PRED_VALUE_RANGE:
+        if kind == MAP_I64_I32:
+            r = lo <= val <= hi
+        else:
+            r = (lo & 0xFFFFFFFFFFFFFFFF) <= val <= (hi & 0xFFFFFFFFFFFFFFFF)
+    elif pred_kind == PRED_KEY_MASK:
+        r = (kbits & (lo & 0xFFFFFFFFFFFFFFFF)) == (hi & 0xFFFFFFFFFFFFFFFF)
+    elif pred_kind == PRED_BLOCK_BOX:
+        x, y, z = (_block_coord(kbits, f) for f in range(3))
+        r = box[0] <= x <= box[1] and box[2] <= y <= box[3] and box[4] <= z <= box[5]
+    else:
+        raise ValueError(f"unknown predicate kind {pred_kind}")
+    return r != bool(negate)

@@ -20,6 +20,8 @@ OK, ERR_ARG, ERR_OOM, ERR_OVERFLOW, ERR_CUDA, ERR_STATE = 0, 1, 2, 3, 4, 5
 RC_NAMES = {0: "HC_OK", 1: "HC_ERR_ARG", 2: "HC_ERR_OOM", 3: "HC_ERR_OVERFLOW", 4: "HC_ERR_CUDA", 5: "HC_ERR_STATE"}
 # per-key status
 INSERTED, EXISTS, OVERFLOW, ERASED, NOT_FOUND = 0, 1, 2, 3, 4
+# selection predicates
+PRED_ALL, PRED_KEY_RANGE, PRED_VALUE_RANGE, PRED_KEY_MASK, PRED_BLOCK_BOX = 0, 1, 2, 3, 4
 # ops, hash modes
 OP_INSERT, OP_FIND, OP_ERASE = 0, 1, 2
 HASH_MIX64, HASH_TESCHNER = 0, 1
@@ -29,7 +31,7 @@ EXPORTS = [
     "hc_get_launch", "hc_insert", "hc_insert_if_absent", "hc_find", "hc_erase", "hc_insert_host", "hc_find_host", "hc_erase_host",
     "hc_size", "hc_stats", "hc_status", "hc_clear", "hc_rehash", "hc_dump", "hc_batch_create",
     "hc_batch_launch", "hc_batch_destroy", "hc_batch_run_noalloc", "hc_measure_random_reads",
-    "hc_batch_scratch_bytes", "hc_batch_run", "hc_device_view_get",
+    "hc_batch_scratch_bytes", "hc_batch_run", "hc_device_view_get", "hc_select",
 ]
 
 
@@ -63,6 +65,12 @@ class BatchItem(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("lane_bytes", ctypes.c_int32), ("keys_per_group", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class Predicate(ctypes.Structure):
+    """hc_predicate: which stored entries hc_select appends."""
+    _fields_ = [("kind", ctypes.c_int32), ("negate", ctypes.c_int32), ("lo", ctypes.c_int64), ("hi", ctypes.c_int64),
+                ("box", ctypes.c_int32 * 6)]
 
 
 class DeviceView(ctypes.Structure):
@@ -108,6 +116,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_batch_scratch_bytes": (i64, [i64]),
         "hc_batch_run": (i32, [P(BatchItem), i64, P(BatchConfig), vp, i64, vp]),
         "hc_device_view_get": (i32, [vp, P(DeviceView), vp]),
+        "hc_select": (i32, [vp, P(Predicate), vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -25,8 +25,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          f"-I{os.path.join(ROOT, 'include')}"]
 
-SOURCES = ["hc_api.cu", "hc_batch.cu", "hc_probe.cu", "hc_kind_set_u32.cu", "hc_kind_set_u64.cu", "hc_kind_map_i64_i32.cu",
-           "hc_kind_map_u64_u64.cu"]
+SOURCES = ["hc_api.cu", "hc_batch.cu", "hc_probe.cu", "hc_select.cu", "hc_kind_set_u32.cu", "hc_kind_set_u64.cu",
+           "hc_kind_map_i64_i32.cu", "hc_kind_map_u64_u64.cu"]
 
 
 def nvcc() -> str:
@@ -37,7 +37,8 @@ def nvcc() -> str:
 
 
 def _deps() -> list[str]:
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "hc.h")]
+    inc = os.path.join(ROOT, "include")
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
 
 
 def _example_deps() -> list[str]:

@@ -537,6 +537,45 @@ hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap, int6
 }
 
 
+hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, void *d_vals_out, int64_t cap,
+                int64_t *d_count, void *stream) {
+    hc_rc rc = check_table(t);
+    if (rc != HC_OK) return rc;
+    if (!pred) return fail(HC_ERR_ARG, "pred is NULL");
+    if (!d_count) return fail(HC_ERR_ARG, "d_count is NULL");
+    if ((rc = check_array(d_count, 8, "d_count")) != HC_OK) return rc;
+    if (cap < 0) return fail(HC_ERR_ARG, "cap must be >= 0");
+    if (pred->kind < HC_PRED_ALL || pred->kind > HC_PRED_BLOCK_BOX)
+        return fail(HC_ERR_ARG, "unknown predicate kind %d", pred->kind);
+    if (pred->negate != 0 && pred->negate != 1) return fail(HC_ERR_ARG, "negate must be 0 or 1");
+    if (pred->kind == HC_PRED_VALUE_RANGE && !is_map(t->kind))
+        return fail(HC_ERR_ARG, "HC_PRED_VALUE_RANGE needs a map");
+    if (pred->kind == HC_PRED_BLOCK_BOX && t->kind == HC_SET_U32)
+        return fail(HC_ERR_ARG, "HC_PRED_BLOCK_BOX needs 64-bit keys");
+    if (cap > 0 && (rc = check_array(d_keys_out, key_bytes(t->kind), "keys output")) != HC_OK) return rc;
+    if (cap > 0 && d_vals_out && is_map(t->kind) &&
+        (rc = check_array(d_vals_out, val_bytes(t->kind), "values output")) != HC_OK)
+        return rc;
+    hc_device_view dv{};
+    dv.buckets = t->view.buckets;
+    dv.header = t->view.hdr;
+    dv.locks = nullptr;
+    dv.nb = t->view.nb;
+    dv.seed = t->view.seed;
+    dv.kind = t->kind;
+    dv.bucket_bytes = t->bucket_bytes;
+    dv.hash_mode = t->view.hash_mode;
+    dv.pad_from = t->view.pad_from;
+    hc::SelectPred p{pred->kind, pred->negate, (long long)pred->lo, (long long)pred->hi, {}};
+    for (int i = 0; i < 6; ++i) p.box[i] = pred->box[i];
+    const cudaError_t e = hc::select_entries(dv, p, d_keys_out, is_map(t->kind) ? d_vals_out : nullptr,
+                                             (unsigned long long)cap, reinterpret_cast<unsigned long long *>(d_count),
+                                             (unsigned long long)t->phys + 2ull, sm_count_of(t->device),
+                                             static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "launching the selection kernel");
+    return HC_OK;
+}
+
 hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream) {
     hc_rc rc = check_table(t);
     if (rc != HC_OK) return rc;

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "hc.h"
+
 namespace hc {
 
 struct View;
@@ -38,5 +40,16 @@ HC_DECLARE_KIND(map_i64_i32)
 HC_DECLARE_KIND(map_u64_u64)
 
 #undef HC_DECLARE_KIND
+
+// hc_predicate as the selection kernel takes it.
+struct SelectPred {
+    int kind, negate;
+    long long lo, hi;
+    int box[6];
+};
+
+// Appends the stored entries of the table behind dv that satisfy p (hc_select).
+cudaError_t select_entries(const hc_device_view &dv, const SelectPred &p, void *ko, void *vo, unsigned long long cap,
+                           unsigned long long *count, unsigned long long positions, int sms, cudaStream_t s);
 
 }  // namespace hc

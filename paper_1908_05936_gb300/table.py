@@ -210,6 +210,31 @@ class Table:
         return status
 
     # ------------------------------------------------------- whole table --
+    def select(self, kind: int = L.PRED_ALL, lo: int = 0, hi: int = 0, box=(0, 0, 0, 0, 0, 0), negate: bool = False,
+               keys_out: torch.Tensor | None = None, vals_out: torch.Tensor | bool | None = True,
+               count: torch.Tensor | None = None, cap: int | None = None, stream=None):
+        """Append the stored entries that satisfy the predicate (hc_select) to
+        keys_out / vals_out through the device int64 `count` (the output's
+        size, 0 when not given).  Returns (keys_out, vals_out, count); no
+        synchronisation.  Bounds wrap to int64 as the C struct holds them."""
+        if cap is None:
+            cap = keys_out.numel() if keys_out is not None else self.size(stream)
+        if keys_out is None:
+            keys_out = torch.empty(cap, dtype=KEY_TORCH[self.key_bytes], device=self.device)
+        if self.is_map and vals_out is True:
+            vals_out = torch.empty(cap, dtype=KEY_TORCH[self.val_bytes], device=self.device)
+        elif not isinstance(vals_out, torch.Tensor) or not self.is_map:
+            vals_out = None
+        if count is None:
+            count = torch.zeros(1, dtype=torch.int64, device=self.device)
+        _check_tensor(count, 8, "count")
+        wrap = lambda x: ((int(x) + 2**63) % 2**64) - 2**63
+        pred = L.Predicate(kind, int(negate), wrap(lo), wrap(hi), (ctypes.c_int32 * 6)(*box))
+        L.check(self.lib.hc_select(self.h, ctypes.byref(pred), keys_out.data_ptr(),
+                                   vals_out.data_ptr() if vals_out is not None else None, cap, count.data_ptr(),
+                                   _stream_handle(stream)))
+        return keys_out, vals_out, count
+
     def device_view(self, stream=None) -> L.DeviceView:
         """The hc_device_view that kernels using include/hc_device.cuh take."""
         dv = L.DeviceView()

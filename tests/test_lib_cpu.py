@@ -51,6 +51,8 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.hc_erase(None, None, 1, None, None) == L.ERR_ARG
     assert lib.hc_destroy(None) == L.OK
     assert lib.hc_batch_create(None, None, 0, None, None) == L.ERR_ARG
+    pred = L.Predicate(L.PRED_ALL, 0, 0, 0)
+    assert lib.hc_select(None, ctypes.byref(pred), None, None, 0, None, None) == L.ERR_ARG
     assert lib.hc_batch_destroy(None) == L.OK
 
 
