@@ -230,6 +230,47 @@ HC_API hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream);
 HC_API hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap,
               int64_t *n_out, void *stream);
 
+/* ---- free-running mixed batches --------------------------------------------
+ * One launch in which inserts, finds and erases of the same table run at
+ * once, one operation per thread (Section 4, "Guarantees": concurrency across
+ * all defined operations), with the in-kernel functions of
+ * include/hc_device.cuh and their contract: for every key the results are
+ * those of some serial order of that key's operations, no key is stored
+ * twice, map values are seen only with their keys, inserts claim EMPTY slots
+ * only (tombstones return with hc_clear / hc_rehash).  No order across keys
+ * and no phase order is implied (the batched form's phases are the ordered
+ * alternative).
+ *   d_ops[i]: 0 insert, 1 find, 2 erase (any other value erases).
+ *   d_status[i] (may be NULL): insert / erase status, or 1 / 0 for a find
+ *     that found / did not find its key.
+ *   d_vals: map values of the inserts (read at insert positions only);
+ *   d_vals_out (maps, may be NULL): values found (0 when absent).
+ * For maps the first call allocates the table's lock bits (as
+ * hc_device_view_get) and synchronises `stream`; otherwise asynchronous. */
+HC_API hc_rc hc_apply_mixed(hc_table *t, const uint8_t *d_ops, const void *d_keys, const void *d_vals, int64_t n,
+                            uint8_t *d_status, void *d_vals_out, void *stream);
+
+/* ---- ordered duplicates: the lowest index wins ---------------------------
+ * Section 4 leaves which of several equal keys of one concurrent call
+ * succeeds to the scheduler (the plain calls report one INSERTED or ERASED
+ * per key, at any of its positions, and a map keeps any one of the equal
+ * keys' values).  The ordered calls give every position the result of
+ * processing the batch sequentially in index order: the first occurrence of
+ * a key probes the container (its value is the one a map stores), every
+ * later occurrence reports EXISTS (OVERFLOW if the first overflowed) for an
+ * insert and NOT_FOUND for an erase.  Which distinct keys overflow a full
+ * table is still unspecified.
+ *
+ * d_scratch: device memory of hc_ordered_scratch_bytes(n) bytes, 256-byte
+ * aligned, owned by the caller, free for reuse once the call's work on
+ * `stream` is done (about 16 bytes per key, plus n bytes).  Asynchronous.
+ * HC_ERR_ARG if the scratch is NULL, misaligned or too small. */
+HC_API int64_t hc_ordered_scratch_bytes(int64_t n);
+HC_API hc_rc hc_insert_ordered(hc_table *t, const void *d_keys, const void *d_vals, int64_t n, uint8_t *d_status,
+                               void *d_scratch, int64_t scratch_bytes, void *stream);
+HC_API hc_rc hc_erase_ordered(hc_table *t, const void *d_keys, int64_t n, uint8_t *d_status, void *d_scratch,
+                              int64_t scratch_bytes, void *stream);
+
 /* ---- selection over the stored entries ----------------------------------
  * Section 3.6 selects, for example, the voxel blocks a camera sees: a range
  * over a container's stored entries, copied with a predicate through a back

@@ -32,6 +32,7 @@ EXPORTS = [
     "hc_size", "hc_stats", "hc_status", "hc_clear", "hc_rehash", "hc_dump", "hc_batch_create",
     "hc_batch_launch", "hc_batch_destroy", "hc_batch_run_noalloc", "hc_measure_random_reads",
     "hc_batch_scratch_bytes", "hc_batch_run", "hc_device_view_get", "hc_select",
+    "hc_ordered_scratch_bytes", "hc_insert_ordered", "hc_erase_ordered", "hc_apply_mixed",
 ]
 
 
@@ -117,6 +118,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_batch_run": (i32, [P(BatchItem), i64, P(BatchConfig), vp, i64, vp]),
         "hc_device_view_get": (i32, [vp, P(DeviceView), vp]),
         "hc_select": (i32, [vp, P(Predicate), vp, vp, i64, vp, vp]),
+        "hc_ordered_scratch_bytes": (i64, [i64]),
+        "hc_insert_ordered": (i32, [vp, vp, vp, i64, vp, vp, i64, vp]),
+        "hc_erase_ordered": (i32, [vp, vp, i64, vp, vp, i64, vp]),
+        "hc_apply_mixed": (i32, [vp, vp, vp, vp, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -537,6 +537,58 @@ hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap, int6
 }
 
 
+int64_t hc_ordered_scratch_bytes(int64_t n) {
+    if (n < 0) return -1;
+    const unsigned long long P = hc::ordered_aux_slots(n);
+    return (int64_t)(((P + (unsigned long long)n) * 8ull + (unsigned long long)n + 255ull) / 256ull * 256ull);
+}
+
+static hc_rc ordered_checks(const hc_table *t, int op, const void *keys, const void *vals, long long n,
+                            const void *scratch, int64_t scratch_bytes) {
+    hc_rc rc = range_checks(t, op, keys, vals, n, nullptr, nullptr);
+    if (rc != HC_OK || n == 0) return rc;
+    if (!scratch) return fail(HC_ERR_ARG, "scratch is NULL");
+    if ((rc = check_array(scratch, 256, "scratch")) != HC_OK) return rc;
+    if (scratch_bytes < hc_ordered_scratch_bytes(n))
+        return fail(HC_ERR_ARG, "scratch of %lld bytes is below the %lld that %lld keys need", (long long)scratch_bytes,
+                    (long long)hc_ordered_scratch_bytes(n), n);
+    return HC_OK;
+}
+
+hc_rc hc_insert_ordered(hc_table *t, const void *d_keys, const void *d_vals, int64_t n, uint8_t *d_status,
+                        void *d_scratch, int64_t scratch_bytes, void *stream) {
+    hc_rc rc = ordered_checks(t, hc::OP_INSERT, d_keys, d_vals, n, d_scratch, scratch_bytes);
+    if (rc != HC_OK || n == 0) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int sms = sm_count_of(t->device);
+    cudaError_t e = hc::ordered_leaders(d_keys, key_bytes(t->kind), n, d_scratch, &t->view.hdr->err, sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "finding the first occurrences");
+    if ((rc = run_range(t, hc::OP_INSERT, d_keys, d_vals, n, d_status, nullptr, s, hc::ordered_skip(n, d_scratch))) !=
+        HC_OK)
+        return rc;
+    if (d_status) {
+        e = hc::ordered_follow_insert(n, d_scratch, d_status, sms, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copying the first occurrences' results");
+    }
+    return HC_OK;
+}
+
+hc_rc hc_erase_ordered(hc_table *t, const void *d_keys, int64_t n, uint8_t *d_status, void *d_scratch,
+                       int64_t scratch_bytes, void *stream) {
+    hc_rc rc = ordered_checks(t, hc::OP_ERASE, d_keys, nullptr, n, d_scratch, scratch_bytes);
+    if (rc != HC_OK || n == 0) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int sms = sm_count_of(t->device);
+    cudaError_t e = hc::ordered_leaders(d_keys, key_bytes(t->kind), n, d_scratch, &t->view.hdr->err, sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "finding the first occurrences");
+    // the streaming erase takes the skip flags (later occurrences: NOT_FOUND)
+    hc::LaunchShape sh{key_region_bytes(t->kind, t->bucket_bytes), 4, 64, 0, sms};
+    e = dispatch_range(t->kind, hc::OP_ERASE, t->view, t->bucket_bytes, d_keys, nullptr, n, d_status, nullptr, sh,
+                       hc::ordered_skip(n, d_scratch), s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the erase kernel");
+    return HC_OK;
+}
+
 hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, void *d_vals_out, int64_t cap,
                 int64_t *d_count, void *stream) {
     hc_rc rc = check_table(t);
@@ -576,11 +628,7 @@ hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, void *d
     return HC_OK;
 }
 
-hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream) {
-    hc_rc rc = check_table(t);
-    if (rc != HC_OK) return rc;
-    if (!out) return fail(HC_ERR_ARG, "out is NULL");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+static hc_rc ensure_locks(hc_table *t, cudaStream_t s) {
     if (is_map(t->kind) && !t->locks) {
         const size_t words = (size_t)((t->view.nb + 31) / 32);
         void *p = nullptr;
@@ -598,6 +646,10 @@ hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream) {
         }
         t->locks = static_cast<uint32_t *>(p);
     }
+    return HC_OK;
+}
+
+static void fill_view(const hc_table *t, hc_device_view *out) {
     out->buckets = t->view.buckets;
     out->header = t->view.hdr;
     out->locks = t->locks;
@@ -607,6 +659,35 @@ hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream) {
     out->bucket_bytes = t->bucket_bytes;
     out->hash_mode = t->view.hash_mode;
     out->pad_from = t->view.pad_from;
+}
+
+hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream) {
+    hc_rc rc = check_table(t);
+    if (rc != HC_OK) return rc;
+    if (!out) return fail(HC_ERR_ARG, "out is NULL");
+    if ((rc = ensure_locks(t, static_cast<cudaStream_t>(stream))) != HC_OK) return rc;
+    fill_view(t, out);
+    return HC_OK;
+}
+
+hc_rc hc_apply_mixed(hc_table *t, const uint8_t *d_ops, const void *d_keys, const void *d_vals, int64_t n,
+                     uint8_t *d_status, void *d_vals_out, void *stream) {
+    hc_rc rc = check_table(t);
+    if (rc != HC_OK) return rc;
+    if (n < 0) return fail(HC_ERR_ARG, "n must be >= 0 (got %lld)", (long long)n);
+    if (n == 0) return HC_OK;
+    if (!d_ops) return fail(HC_ERR_ARG, "ops array is NULL");
+    if ((rc = check_array(d_keys, key_bytes(t->kind), "keys")) != HC_OK) return rc;
+    if (is_map(t->kind) && (rc = check_array(d_vals, val_bytes(t->kind), "values")) != HC_OK) return rc;
+    if (d_vals_out && is_map(t->kind) && (rc = check_array(d_vals_out, val_bytes(t->kind), "values output")) != HC_OK)
+        return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_locks(t, s)) != HC_OK) return rc;
+    hc_device_view dv{};
+    fill_view(t, &dv);
+    const cudaError_t e = hc::mixed_ops(dv, d_ops, d_keys, is_map(t->kind) ? d_vals : nullptr, n, d_status,
+                                        is_map(t->kind) ? d_vals_out : nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the mixed kernel");
     return HC_OK;
 }
 

@@ -48,6 +48,17 @@ struct SelectPred {
     int box[6];
 };
 
+// Ordered calls (hc_ordered.cu): scratch layout and the leader passes.
+unsigned long long ordered_aux_slots(long long n);
+cudaError_t ordered_leaders(const void *keys, int key_bytes, long long n, void *scratch, unsigned *err, int sms,
+                            cudaStream_t s);
+cudaError_t ordered_follow_insert(long long n, void *scratch, uint8_t *status, int sms, cudaStream_t s);
+const uint8_t *ordered_skip(long long n, const void *scratch);
+
+// One free-running launch of per-thread insert / find / erase (hc_mixed.cu).
+cudaError_t mixed_ops(const hc_device_view &dv, const uint8_t *ops, const void *keys, const void *vals, long long n,
+                      uint8_t *status, void *vals_out, cudaStream_t s);
+
 // Appends the stored entries of the table behind dv that satisfy p (hc_select).
 cudaError_t select_entries(const hc_device_view &dv, const SelectPred &p, void *ko, void *vo, unsigned long long cap,
                            unsigned long long *count, unsigned long long positions, int sms, cudaStream_t s);

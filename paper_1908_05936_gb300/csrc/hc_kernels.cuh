@@ -252,12 +252,13 @@ cudaError_t launch_insert_stream(const View &v, const void *keys, const void *va
 }
 
 template <int KIND, int BB, int KPT, int S>
-cudaError_t launch_erase_stream(const View &v, const void *keys, long long n, uint8_t *out, int block, cudaStream_t s) {
+cudaError_t launch_erase_stream(const View &v, const void *keys, long long n, uint8_t *out, const uint8_t *skip,
+                                int block, cudaStream_t s) {
     using T = Traits<KIND>;
     const long long chunk = (long long)block * KPT;
     const unsigned grid = (unsigned)((n + chunk - 1) / chunk);
     const size_t smem = (size_t)chunk * (sizeof(typename T::Key) + 1);
-    k_erase_stream<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys, n, out);
+    k_erase_stream<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys, n, out, skip);
     return cudaGetLastError();
 }
 
@@ -274,8 +275,8 @@ cudaError_t launch_range_kpt(int op, const View &v, const void *keys, const void
                 if (sh.keys_per_group == 4) return launch_insert_stream<KIND, BB, 4, 2>(v, keys, vals, n, out, skip, sh.block, s);
                 if (sh.keys_per_group == 8) return launch_insert_stream<KIND, BB, 8, 4>(v, keys, vals, n, out, skip, sh.block, s);
             } else {
-                if (sh.keys_per_group == 4) return launch_erase_stream<KIND, BB, 4, 2>(v, keys, n, out, sh.block, s);
-                if (sh.keys_per_group == 8) return launch_erase_stream<KIND, BB, 8, 4>(v, keys, n, out, sh.block, s);
+                if (sh.keys_per_group == 4) return launch_erase_stream<KIND, BB, 4, 2>(v, keys, n, out, skip, sh.block, s);
+                if (sh.keys_per_group == 8) return launch_erase_stream<KIND, BB, 8, 4>(v, keys, n, out, skip, sh.block, s);
             }
         }
         return cudaErrorInvalidValue;

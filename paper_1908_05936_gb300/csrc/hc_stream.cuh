@@ -282,10 +282,12 @@ k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename T
 // finds its key joins the round's compare-and-swap (key -> TOMB) with the
 // other slots that found theirs.  A failed swap means an equal key of the
 // same call erased the slot first: that key reports ERASED, this one
-// NOT_FOUND, as in the lock-step form.
+// NOT_FOUND, as in the lock-step form.  Keys flagged in `skip` report
+// NOT_FOUND without a probe (the later occurrences of a key in the ordered
+// erase).
 template <int KIND, int BB, int KPT, int S>
 __global__ void __launch_bounds__(256, HC_STREAM_ERASE_MINB)
-k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status) {
+k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status, const uint8_t *skip) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Sl = Slots<KIND, BB>;
@@ -299,7 +301,10 @@ k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint
 
     const long long c0 = (long long)blockIdx.x * chunk;
     const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
-    for (int i = threadIdx.x; i < m; i += nt) sk[i] = ld_stream(keys + c0 + i);
+    for (int i = threadIdx.x; i < m; i += nt) {
+        sk[i] = ld_stream(keys + c0 + i);
+        ss[i] = (skip && ld_stream(skip + c0 + i)) ? (uint8_t)ST_NOT_FOUND : (uint8_t)0xFF;   // 0xFF: to do
+    }
     __syncthreads();
 
     Counts cnt;
@@ -313,6 +318,7 @@ k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint
         while (next < KPT) {
             const int i = threadIdx.x + (next++) * nt;
             if (i >= m) { next = KPT; break; }
+            if (ss[i] != 0xFF) continue;                       // a later occurrence: NOT_FOUND
             const Key k = sk[i];
             const int side = side_index<KIND>(k);
             if (side >= 0) {                                   // key equal to a marker: side slot

@@ -140,6 +140,72 @@ class Table:
                                              _stream_handle(stream)))
         return status
 
+    def apply_mixed(self, ops: torch.Tensor, keys: torch.Tensor, vals: torch.Tensor | None = None,
+                    status: torch.Tensor | bool = True, vals_out: torch.Tensor | bool = False, stream=None):
+        """Free-running mixed batch (hc_apply_mixed): ops[i] 0 insert, 1 find,
+        2 erase, all at once.  Returns (status, vals_out or None)."""
+        _check_tensor(ops, 1, "ops")
+        _check_tensor(keys, self.key_bytes, "keys")
+        n = keys.numel()
+        if ops.numel() != n:
+            raise ValueError("ops and keys differ in length")
+        if self.is_map:
+            _check_tensor(vals, self.val_bytes, "vals")
+        if status is True:
+            status = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        elif status is False:
+            status = None
+        if self.is_map and vals_out is True:
+            vals_out = torch.empty(n, dtype=KEY_TORCH[self.val_bytes], device=keys.device)
+        elif not isinstance(vals_out, torch.Tensor) or not self.is_map:
+            vals_out = None
+        L.check(self.lib.hc_apply_mixed(self.h, ops.data_ptr(), keys.data_ptr(),
+                                        vals.data_ptr() if self.is_map else None, n,
+                                        status.data_ptr() if status is not None else None,
+                                        vals_out.data_ptr() if vals_out is not None else None, _stream_handle(stream)))
+        return status, vals_out
+
+    def _scratch(self, n: int, scratch: torch.Tensor | None) -> torch.Tensor:
+        need = int(self.lib.hc_ordered_scratch_bytes(n))
+        if scratch is None or scratch.numel() < need:
+            scratch = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+        return scratch
+
+    def insert_ordered(self, keys: torch.Tensor, vals: torch.Tensor | None = None, status: torch.Tensor | bool = True,
+                       scratch: torch.Tensor | None = None, stream=None) -> torch.Tensor | None:
+        """Insert where the lowest index wins among equal keys (every position
+        gets the result of a sequential pass in index order)."""
+        _check_tensor(keys, self.key_bytes, "keys")
+        n = keys.numel()
+        if self.is_map:
+            _check_tensor(vals, self.val_bytes, "vals")
+        if status is True:
+            status = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        elif status is False:
+            status = None
+        sc = self._scratch(n, scratch)
+        base = (sc.data_ptr() + 255) // 256 * 256
+        L.check(self.lib.hc_insert_ordered(self.h, keys.data_ptr(), vals.data_ptr() if self.is_map else None, n,
+                                           status.data_ptr() if status is not None else None, base,
+                                           sc.numel() - (base - sc.data_ptr()), _stream_handle(stream)))
+        return status
+
+    def erase_ordered(self, keys: torch.Tensor, status: torch.Tensor | bool = True, scratch: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor | None:
+        """Erase where the first occurrence of a key erases it and later ones
+        report NOT_FOUND."""
+        _check_tensor(keys, self.key_bytes, "keys")
+        n = keys.numel()
+        if status is True:
+            status = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        elif status is False:
+            status = None
+        sc = self._scratch(n, scratch)
+        base = (sc.data_ptr() + 255) // 256 * 256
+        L.check(self.lib.hc_erase_ordered(self.h, keys.data_ptr(), n, status.data_ptr() if status is not None else None,
+                                          base, sc.numel() - (base - sc.data_ptr()), _stream_handle(stream)))
+        return status
+
     def find(self, keys: torch.Tensor, found: torch.Tensor | None = None, vals_out: torch.Tensor | bool | None = True,
              stream=None):
         _check_tensor(keys, self.key_bytes, "keys")

@@ -188,6 +188,38 @@ def test_free_running_mixed_ops(kind, bb):
         t.close()
 
 
+@pytest.mark.parametrize("kind", KINDS)
+def test_apply_mixed_serial_order_per_key(kind):
+    """hc_apply_mixed (the library's free-running mixed batch) under the same
+    per-key check, with 2^20 operations over 2^14 keys."""
+    rng = np.random.default_rng(750 + kind)
+    t = Table(kind, 1 << 21, bucket_bytes=64)
+    dom = random_keys(kind, 1 << 14, rng)
+    dom = dom[np.unique(C.bits(dom), return_index=True)[1]]
+    try:
+        before = set()
+        for rep in range(2):
+            n = 1 << 20
+            keys = dom[rng.integers(0, len(dom), size=n)]
+            ops = rng.choice(np.array([0, 1, 2], dtype=np.uint8), size=n, p=[0.5, 0.25, 0.25])
+            vals = value_for(kind, keys)
+            st, vo = t.apply_mixed(to_device(ops), to_device(keys), to_device(vals) if vals is not None else None,
+                                   vals_out=t.is_map)
+            st = to_numpy(st, np.uint8)
+            gk, gv = t.dump_numpy()
+            kb = C.bits(gk)
+            assert len(np.unique(kb)) == len(kb) == t.size()
+            after = {int(x) for x in kb}
+            assert LZ.check_history(C.bits(keys), ops, st, before, after) == []
+            if t.is_map:
+                found = (ops == 1) & (st == 1)
+                assert np.array_equal(C.bits(to_numpy(vo, O.VAL_DTYPE[kind])[found]), C.bits(vals[found]))
+            assert t.status() == L.OK
+            before = after
+    finally:
+        t.close()
+
+
 def _pack21(x, y, z):
     m = np.int64(0x1FFFFF)
     return ((x & m) | ((y & m) << 21) | ((z & m) << 42)).astype(np.int64)

@@ -51,6 +51,11 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.hc_erase(None, None, 1, None, None) == L.ERR_ARG
     assert lib.hc_destroy(None) == L.OK
     assert lib.hc_batch_create(None, None, 0, None, None) == L.ERR_ARG
+    assert lib.hc_ordered_scratch_bytes(-1) == -1
+    assert lib.hc_ordered_scratch_bytes(1000) >= 2048 * 8 + 1000 * 9
+    assert lib.hc_insert_ordered(None, None, None, 1, None, None, 0, None) == L.ERR_ARG
+    assert lib.hc_erase_ordered(None, None, 1, None, None, 0, None) == L.ERR_ARG
+    assert lib.hc_apply_mixed(None, None, None, None, 1, None, None, None) == L.ERR_ARG
     pred = L.Predicate(L.PRED_ALL, 0, 0, 0)
     assert lib.hc_select(None, ctypes.byref(pred), None, None, 0, None, None) == L.ERR_ARG
     assert lib.hc_batch_destroy(None) == L.OK
