@@ -374,6 +374,9 @@ public:
         }
     }
 
+    __host__ __device__ int bucket_bytes() const { return bb_; }
+    __host__ __device__ const hc::View &view() const { return v_; }
+
     // Number of positions: every slot of the table, then the two side slots.
     __device__ long long positions() const { return (long long)(v_.nb * (unsigned long long)spb()) + 2; }
 
@@ -424,45 +427,117 @@ private:
     int bb_;
 };
 
-// Selection over the stored entries (Section 3.6's block selection: a range
-// over a container, copied with a predicate through a back inserter into a
-// vector).  Appends every stored (key, value) with
-// pred(key, value) true to keys_out / vals_out (vals_out may be NULL; sets
-// pass NULL) through *size, the output vector's element count: an entry's
-// position is the count before it, entries at positions >= cap are counted
-// but not written.  Every thread of the calling grid calls it with the same
-// arguments; blocks must be one-dimensional whole warps.  Each warp walks the
-// positions in steps of 32 and appends its matches with one atomic add.  No
-// insert or erase may run on the table meanwhile.
-template <int KIND, class Pred>
-__device__ void copy_if(const Table<KIND> &t, Pred pred, typename Table<KIND>::Key *keys_out,
-                        typename Table<KIND>::Val *vals_out, unsigned long long cap, unsigned long long *size) {
-    using Key = typename Table<KIND>::Key;
-    using Val = typename Table<KIND>::Val;
-    const unsigned lane = detail::lane_id();
-    const long long total = t.positions();
-    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
-    const long long w = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    for (long long base = w * 32; base < total; base += warps * 32) {
-        const long long pos = base + lane;
-        Key k{};
-        Val v{};
-        bool hit = false;
-        if (pos < total && t.entry(pos, &k, Table<KIND>::is_map ? &v : nullptr)) hit = pred(k, v);
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (!m) continue;
-        unsigned long long first = 0;
-        if (lane == 0) first = atomicAdd(size, (unsigned long long)__popc(m));
-        first = __shfl_sync(0xffffffffu, first, 0);
-        if (hit) {
-            const unsigned long long at = first + __popc(m & ((1u << lane) - 1u));
-            if (at < cap) {
-                keys_out[at] = k;
-                if constexpr (Table<KIND>::is_map) {
-                    if (vals_out) vals_out[at] = v;
+namespace detail {
+
+// Keys (and values) of a block tile of J * blockDim.x consecutive slot
+// positions: thread t holds positions t, t + blockDim.x, ...; the matches
+// of the tile are numbered by a block-wide prefix sum and appended with one
+// atomic add on *size.
+template <int KIND, int BB, class Pred>
+__device__ void copy_if_bb(const View &v, Pred pred, typename hc::Traits<KIND>::Key *keys_out,
+                           typename hc::Traits<KIND>::Val *vals_out, unsigned long long cap, unsigned long long *size) {
+    using T = hc::Traits<KIND>;
+    using Key = typename T::Key;
+    using Val = typename T::Val;
+    using S = hc::Slots<KIND, BB>;
+    constexpr int J = 8;
+    __shared__ unsigned warp_sum[32];
+    __shared__ unsigned long long tile_base;
+    const unsigned lane = lane_id();
+    const unsigned warp = threadIdx.x / 32;
+    const unsigned nwarps = blockDim.x / 32;
+    const unsigned long long phys = v.nb * (unsigned long long)S::SPB;
+    const unsigned long long tile = (unsigned long long)blockDim.x * J;
+    for (unsigned long long t0 = (unsigned long long)blockIdx.x * tile; t0 < phys; t0 += (unsigned long long)gridDim.x * tile) {
+        Key k[J];
+        Val val[J];
+        uint32_t hit = 0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const unsigned long long pos = t0 + (unsigned long long)j * blockDim.x + threadIdx.x;
+            val[j] = Val();
+            if (pos < phys) {
+                const unsigned long long b = pos / S::SPB;
+                const int q = (int)(pos % S::SPB);
+                k[j] = __ldcs(reinterpret_cast<const Key *>(S::key(v, b, q)));
+                if (k[j] != T::EMPTY && k[j] != T::TOMB) {
+                    if constexpr (T::MAP) val[j] = __ldcs(reinterpret_cast<const Val *>(S::val(v, b, q)));
+                    hit |= (uint32_t)pred(k[j], val[j]) << j;
                 }
             }
         }
+        // exclusive offset of this thread's matches inside the tile
+        const unsigned mine = __popc(hit);
+        unsigned incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned run = 0;
+            for (unsigned w = 0; w < nwarps; ++w) {
+                const unsigned c = warp_sum[w];
+                warp_sum[w] = run;
+                run += c;
+            }
+            tile_base = run ? atomicAdd(size, (unsigned long long)run) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long at = tile_base + warp_sum[warp] + (incl - mine);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            if (hit >> j & 1u) {
+                if (at < cap) {
+                    keys_out[at] = k[j];
+                    if constexpr (T::MAP) {
+                        if (vals_out) vals_out[at] = val[j];
+                    }
+                }
+                ++at;
+            }
+        }
+        __syncthreads();                               // warp_sum and tile_base are reused
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {         // the two side slots
+        for (int side = 0; side < 2; ++side) {
+            if (!*((volatile unsigned int *)&v.hdr->side_present[side])) continue;
+            const Key k = side == 0 ? T::EMPTY : T::TOMB;
+            const Val val = T::MAP ? (Val) * ((volatile unsigned long long *)&v.hdr->side_val[side]) : Val();
+            if (!pred(k, val)) continue;
+            const unsigned long long at = atomicAdd(size, 1ull);
+            if (at < cap) {
+                keys_out[at] = k;
+                if constexpr (T::MAP) {
+                    if (vals_out) vals_out[at] = val;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace detail
+
+// Selection over the stored entries (Section 3.6's block selection: a range
+// over a container, copied with a predicate through a back inserter into a
+// vector).  Appends every stored (key, value) with pred(key, value) true to
+// keys_out / vals_out (vals_out may be NULL; sets pass NULL) through *size,
+// the output vector's element count: an entry's position is the count before
+// it, entries at positions >= cap are counted but not written.  Every thread
+// of every block of the calling grid calls it with the same arguments (it
+// synchronises the block); blocks are one-dimensional, whole warps, at most
+// 1024 threads.  A block walks tiles of 8 * blockDim.x slot positions and
+// appends a tile's matches with one atomic add.  No insert or erase may run
+// on the table meanwhile.
+template <int KIND, class Pred>
+__device__ void copy_if(const Table<KIND> &t, Pred pred, typename Table<KIND>::Key *keys_out,
+                        typename Table<KIND>::Val *vals_out, unsigned long long cap, unsigned long long *size) {
+    switch (t.bucket_bytes()) {
+        case 32: detail::copy_if_bb<KIND, 32>(t.view(), pred, keys_out, vals_out, cap, size); break;
+        case 64: detail::copy_if_bb<KIND, 64>(t.view(), pred, keys_out, vals_out, cap, size); break;
+        default: detail::copy_if_bb<KIND, 128>(t.view(), pred, keys_out, vals_out, cap, size); break;
     }
 }
 

@@ -503,6 +503,8 @@ hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
     return HC_OK;
 }
 
+static void fill_view(const hc_table *t, hc_device_view *out);
+
 hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap, int64_t *n_out, void *stream) {
     hc_rc rc = check_table(t);
     if (rc != HC_OK) return rc;
@@ -515,17 +517,13 @@ hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap, int6
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_set_u64<<<1, 1, 0, s>>>(&t->view.hdr->dump_count, 0ull);
     HC_CUDA(cudaGetLastError(), "resetting the dump cursor");
-    const int sms = sm_count_of(t->device);
-    void *vo = is_map(t->kind) ? d_vals_out : nullptr;
-    cudaError_t e;
-    switch (t->kind) {
-        case HC_SET_U32: e = hc::set_u32_dump(t->view, t->phys, d_keys_out, vo, cap, t->bucket_bytes, sms, s); break;
-        case HC_SET_U64: e = hc::set_u64_dump(t->view, t->phys, d_keys_out, vo, cap, t->bucket_bytes, sms, s); break;
-        case HC_MAP_I64_I32:
-            e = hc::map_i64_i32_dump(t->view, t->phys, d_keys_out, vo, cap, t->bucket_bytes, sms, s);
-            break;
-        default: e = hc::map_u64_u64_dump(t->view, t->phys, d_keys_out, vo, cap, t->bucket_bytes, sms, s); break;
-    }
+    // the selection of every stored entry, appended through the header's cursor
+    hc_device_view dv{};
+    fill_view(t, &dv);
+    const hc::SelectPred all{HC_PRED_ALL, 0, 0, 0, {}};
+    const cudaError_t e = hc::select_entries(dv, all, d_keys_out, is_map(t->kind) ? d_vals_out : nullptr,
+                                             (unsigned long long)cap, &t->view.hdr->dump_count,
+                                             (unsigned long long)t->phys + 2ull, sm_count_of(t->device), s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the dump kernel");
     hc::Header h;
     if ((rc = read_header(t, &h, s)) != HC_OK) return rc;
@@ -609,15 +607,7 @@ hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, void *d
         (rc = check_array(d_vals_out, val_bytes(t->kind), "values output")) != HC_OK)
         return rc;
     hc_device_view dv{};
-    dv.buckets = t->view.buckets;
-    dv.header = t->view.hdr;
-    dv.locks = nullptr;
-    dv.nb = t->view.nb;
-    dv.seed = t->view.seed;
-    dv.kind = t->kind;
-    dv.bucket_bytes = t->bucket_bytes;
-    dv.hash_mode = t->view.hash_mode;
-    dv.pad_from = t->view.pad_from;
+    fill_view(t, &dv);
     hc::SelectPred p{pred->kind, pred->negate, (long long)pred->lo, (long long)pred->hi, {}};
     for (int i = 0; i < 6; ++i) p.box[i] = pred->box[i];
     const cudaError_t e = hc::select_entries(dv, p, d_keys_out, is_map(t->kind) ? d_vals_out : nullptr,

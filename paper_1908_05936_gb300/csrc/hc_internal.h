@@ -29,8 +29,6 @@ struct LaunchShape {
                              cudaStream_t s);                                                                       \
     cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int bb, int sms,       \
                              cudaStream_t s);                                                                       \
-    cudaError_t NAME##_dump(const View &v, unsigned long long phys, void *ko, void *vo, unsigned long long cap,     \
-                            int bb, int sms, cudaStream_t s);                                                       \
     cudaError_t NAME##_rehash(const View &ov, unsigned long long ophys, const View &nv, int bb, int sms,            \
                               cudaStream_t s);
 

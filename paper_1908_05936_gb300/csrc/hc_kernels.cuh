@@ -1,5 +1,5 @@
 // hc_kernels.cuh -- the one-launch-per-call kernels (insert, find, erase,
-// clear, dump, rehash) and their launchers, instantiated once per container
+// clear, rehash) and their launchers, instantiated once per container
 // kind by hc_kind_*.cu.
 #pragma once
 
@@ -93,56 +93,6 @@ __global__ void k_pad_tombstones(View v, unsigned long long first, unsigned long
     if (i < count) {
         const unsigned long long slot = first + i;
         *reinterpret_cast<typename T::Key *>(S::key(v, slot / S::SPB, (int)(slot % S::SPB))) = T::TOMB;
-    }
-}
-
-// ----------------------------------------------------------------- dump ---
-// Stored (key, value) pairs appended to the output through one atomic add per
-// warp on the header's cursor.
-
-template <int KIND, int BB>
-__global__ void __launch_bounds__(256)
-k_dump(View v, unsigned long long phys, typename Traits<KIND>::Key *keys_out, typename Traits<KIND>::Val *vals_out,
-       unsigned long long cap) {
-    using T = Traits<KIND>;
-    using Key = typename T::Key;
-    using S = Slots<KIND, BB>;
-    const int lane = threadIdx.x & 31;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    // whole-warp steps so that every lane reaches the shuffles
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-         base < phys; base += stride) {
-        const unsigned long long i = base + lane;
-        const unsigned long long b = i / S::SPB;
-        const int sl = (int)(i % S::SPB);
-        const Key key = i < phys ? *reinterpret_cast<const Key *>(S::key(v, b, sl)) : T::EMPTY;
-        const bool live = key != T::EMPTY && key != T::TOMB;
-        const unsigned m = __ballot_sync(0xffffffffu, live);
-        if (!m) continue;
-        unsigned long long pos0 = 0;
-        if (lane == 0) pos0 = atomicAdd(&v.hdr->dump_count, (unsigned long long)__popc(m));
-        pos0 = __shfl_sync(0xffffffffu, pos0, 0);
-        if (live) {
-            const unsigned long long pos = pos0 + __popc(m & ((1u << lane) - 1u));
-            if (pos < cap) {
-                keys_out[pos] = key;
-                if constexpr (T::MAP) {
-                    if (vals_out) vals_out[pos] = *reinterpret_cast<const typename T::Val *>(S::val(v, b, sl));
-                }
-            }
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x < 2) {
-        const int s = threadIdx.x;
-        if (v.hdr->side_present[s]) {
-            const unsigned long long pos = atomicAdd(&v.hdr->dump_count, 1ull);
-            if (pos < cap) {
-                keys_out[pos] = s == 0 ? T::EMPTY : T::TOMB;
-                if constexpr (T::MAP) {
-                    if (vals_out) vals_out[pos] = (typename T::Val)v.hdr->side_val[s];
-                }
-            }
-        }
     }
 }
 
@@ -344,23 +294,6 @@ cudaError_t launch_clear(const View &v, unsigned long long phys, unsigned long l
 }
 
 template <int KIND>
-cudaError_t launch_dump(const View &v, unsigned long long phys, void *keys_out, void *vals_out, unsigned long long cap,
-                        int bucket_bytes, int sm_count, cudaStream_t s) {
-    using T = Traits<KIND>;
-    unsigned grid = (unsigned)std::min<unsigned long long>((phys + 255) / 256, (unsigned long long)sm_count * 8);
-    if (grid == 0) grid = 1;
-    auto ko = (typename T::Key *)keys_out;
-    auto vo = (typename T::Val *)vals_out;
-    switch (bucket_bytes) {
-        case 32: k_dump<KIND, 32><<<grid, 256, 0, s>>>(v, phys, ko, vo, cap); break;
-        case 64: k_dump<KIND, 64><<<grid, 256, 0, s>>>(v, phys, ko, vo, cap); break;
-        case 128: k_dump<KIND, 128><<<grid, 256, 0, s>>>(v, phys, ko, vo, cap); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-template <int KIND>
 cudaError_t launch_rehash(const View &old_v, unsigned long long old_phys, const View &new_v, int bucket_bytes,
                           int sm_count, cudaStream_t s) {
     unsigned grid = (unsigned)std::min<unsigned long long>((old_phys + 255) / 256, (unsigned long long)sm_count * 16);
@@ -387,10 +320,6 @@ cudaError_t launch_rehash(const View &old_v, unsigned long long old_phys, const 
     cudaError_t NAME##_clear(const View &v, unsigned long long phys, unsigned long long cap, int bb, int sms,       \
                              cudaStream_t s) {                                                                      \
         return launch_clear<KIND>(v, phys, cap, bb, sms, s);                                                        \
-    }                                                                                                               \
-    cudaError_t NAME##_dump(const View &v, unsigned long long phys, void *ko, void *vo, unsigned long long cap,     \
-                            int bb, int sms, cudaStream_t s) {                                                      \
-        return launch_dump<KIND>(v, phys, ko, vo, cap, bb, sms, s);                                                 \
     }                                                                                                               \
     cudaError_t NAME##_rehash(const View &ov, unsigned long long ophys, const View &nv, int bb, int sms,            \
                               cudaStream_t s) {                                                                     \

@@ -1,7 +1,7 @@
 // hc_select.cu -- selection over the stored entries (Section 3.6): the
 // library's predicates applied through hcd::copy_if of the in-kernel header,
-// one grid that walks every slot position and appends matches with one
-// atomic per warp.
+// one grid whose blocks walk tiles of slot positions and append a tile's
+// matches with one atomic.  hc_dump is the selection of every entry.
 #include <algorithm>
 #include <cstdint>
 
@@ -61,9 +61,9 @@ template <int KIND>
 cudaError_t launch(const hc_device_view &dv, const SelectPred &p, void *ko, void *vo, unsigned long long cap,
                    unsigned long long *count, unsigned long long positions, int sms, cudaStream_t s) {
     using T = Traits<KIND>;
-    const unsigned long long warps = (positions + 31) / 32;
+    const unsigned long long tiles = (positions + 2047) / 2048;   // 8 positions per thread of a 256-thread block
     const unsigned grid = (unsigned)std::max<unsigned long long>(
-        1ull, std::min<unsigned long long>((warps + 7) / 8, (unsigned long long)sms * 8));
+        1ull, std::min<unsigned long long>(tiles, (unsigned long long)sms * 8));
     k_select<KIND><<<grid, 256, 0, s>>>(dv, Selector<KIND>{p}, (typename T::Key *)ko, (typename T::Val *)vo, cap,
                                         count);
     return cudaGetLastError();
