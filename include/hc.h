@@ -89,8 +89,12 @@ enum { HC_OP_INSERT = 0, HC_OP_FIND = 1, HC_OP_ERASE = 2 };
  * 4.1 (coordinates times 73856093, 19349669, 83492791, combined by xor,
  * reduced modulo the bucket count) applied to keys that pack three signed
  * 21-bit block coordinates as x | y << 21 | z << 42 (HC_MAP_I64_I32 only).
- * The hash never changes a result, only where keys are stored. */
-enum { HC_HASH_MIX64 = 0, HC_HASH_TESCHNER = 1 };
+ * HC_HASH_TESCHNER_SHORT3 is the same hash on the paper's own key type, a
+ * short3 of signed 16-bit block coordinates, packed into the 8-byte slot as
+ * (uint16)x | (uint16)y << 16 | (uint16)z << 32 (hc_pack_short3;
+ * HC_MAP_I64_I32 only).  The hash never changes a result, only where keys
+ * are stored. */
+enum { HC_HASH_MIX64 = 0, HC_HASH_TESCHNER = 1, HC_HASH_TESCHNER_SHORT3 = 2 };
 
 /* Layout chosen at creation.  Zero fields take the defaults.  Keys live in an
  * array of buckets; maps keep their values in a parallel array, so a probe
@@ -230,6 +234,18 @@ HC_API hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream);
 HC_API hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap,
               int64_t *n_out, void *stream);
 
+/* ---- short3 keys ----------------------------------------------------------
+ * Section 4.1's voxel-block map is keyed by short3 (three signed 16-bit
+ * block coordinates, 6 bytes).  A map<int64, int32> created with
+ * HC_HASH_TESCHNER_SHORT3 keeps such keys packed into its 8-byte slots as
+ * (uint16)x | (uint16)y << 16 | (uint16)z << 32 (bits 48-63 zero, so a packed
+ * key is never a side-slot pattern) and hashes them with the paper's spatial
+ * hash on the three coordinates.  These calls convert device arrays of n
+ * short3 (int16 x, y, z consecutive, 2-byte aligned, 6 bytes per key) to and
+ * from packed keys (8-byte aligned int64).  Asynchronous on `stream`. */
+HC_API hc_rc hc_pack_short3(const int16_t *d_xyz, int64_t n, int64_t *d_keys, void *stream);
+HC_API hc_rc hc_unpack_short3(const int64_t *d_keys, int64_t n, int16_t *d_xyz, void *stream);
+
 /* ---- free-running mixed batches --------------------------------------------
  * One launch in which inserts, finds and erases of the same table run at
  * once, one operation per thread (Section 4, "Guarantees": concurrency across
@@ -285,10 +301,12 @@ typedef enum hc_pred_kind {
     HC_PRED_VALUE_RANGE = 2,  /* maps: lo <= value <= hi in the value type, uint64 or
                                  int32 (lo/hi as int64)                               */
     HC_PRED_KEY_MASK = 3,     /* (key & lo) == hi on the key's bits                   */
-    HC_PRED_BLOCK_BOX = 4     /* 64-bit keys packing three signed 21-bit block
+    HC_PRED_BLOCK_BOX = 4,    /* 64-bit keys packing three signed 21-bit block
                                  coordinates x | y << 21 | z << 42 (Section 4.1's
                                  voxel blocks): box[0] <= x <= box[1],
                                  box[2] <= y <= box[3], box[4] <= z <= box[5]        */
+    HC_PRED_SHORT3_BOX = 5    /* the same box on packed short3 keys
+                                 (uint16)x | (uint16)y << 16 | (uint16)z << 32       */
 } hc_pred_kind;
 
 typedef struct hc_predicate {
@@ -306,8 +324,8 @@ typedef struct hc_predicate {
  * are counted but not written (the caller sees *d_count > cap).  Order of the
  * appended entries is unspecified.  Asynchronous on `stream`; no insert or
  * erase may run on the table meanwhile.  HC_ERR_ARG for a NULL d_count or
- * pred, an unknown predicate kind, HC_PRED_VALUE_RANGE on a set, or
- * HC_PRED_BLOCK_BOX on HC_SET_U32. */
+ * pred, an unknown predicate kind, HC_PRED_VALUE_RANGE on a set, or a box
+ * predicate on HC_SET_U32. */
 HC_API hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, void *d_vals_out, int64_t cap,
                        int64_t *d_count, void *stream);
 

@@ -27,7 +27,7 @@ LIB = os.path.join(BUILD, "liboracle.so")
 SET_U32, SET_U64, MAP_I64_I32, MAP_U64_U64 = 0, 1, 2, 3
 INSERTED, EXISTS, OVERFLOW, ERASED, NOT_FOUND = 0, 1, 2, 3, 4
 
-PRED_ALL, PRED_KEY_RANGE, PRED_VALUE_RANGE, PRED_KEY_MASK, PRED_BLOCK_BOX = 0, 1, 2, 3, 4
+PRED_ALL, PRED_KEY_RANGE, PRED_VALUE_RANGE, PRED_KEY_MASK, PRED_BLOCK_BOX, PRED_SHORT3_BOX = 0, 1, 2, 3, 4, 5
 
 KEY_DTYPE = {SET_U32: np.uint32, SET_U64: np.uint64, MAP_I64_I32: np.int64, MAP_U64_U64: np.uint64}
 VAL_DTYPE = {MAP_I64_I32: np.int32, MAP_U64_U64: np.uint64}
@@ -185,6 +185,13 @@ def _block_coord(key_bits: int, field: int) -> int:
     return c - (1 << 21) if c >= (1 << 20) else c
 
 
+def _short_coord(key_bits: int, field: int) -> int:
+    """Signed 16-bit field `field` of a packed short3 key (Section 4.1's
+    block coordinates as (uint16)x | (uint16)y << 16 | (uint16)z << 32)."""
+    c = (key_bits >> (16 * field)) & 0xFFFF
+    return c - (1 << 16) if c >= (1 << 15) else c
+
+
 def selected(kind: int, pred_kind: int, lo: int, hi: int, box, negate: bool, key: int, val) -> bool:
     """One entry against one predicate.  `key` and `val` are the entry's
     values in the container's own types (int64 keys and int32 values signed,
@@ -208,6 +215,9 @@ def selected(kind: int, pred_kind: int, lo: int, hi: int, box, negate: bool, key
         r = (kbits & (lo & 0xFFFFFFFFFFFFFFFF)) == (hi & 0xFFFFFFFFFFFFFFFF)
     elif pred_kind == PRED_BLOCK_BOX:
         x, y, z = (_block_coord(kbits, f) for f in range(3))
+        r = box[0] <= x <= box[1] and box[2] <= y <= box[3] and box[4] <= z <= box[5]
+    elif pred_kind == PRED_SHORT3_BOX:
+        x, y, z = (_short_coord(kbits, f) for f in range(3))
         r = box[0] <= x <= box[1] and box[2] <= y <= box[3] and box[4] <= z <= box[5]
     else:
         raise ValueError(f"unknown predicate kind {pred_kind}")

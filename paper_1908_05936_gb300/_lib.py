@@ -21,10 +21,10 @@ RC_NAMES = {0: "HC_OK", 1: "HC_ERR_ARG", 2: "HC_ERR_OOM", 3: "HC_ERR_OVERFLOW", 
 # per-key status
 INSERTED, EXISTS, OVERFLOW, ERASED, NOT_FOUND = 0, 1, 2, 3, 4
 # selection predicates
-PRED_ALL, PRED_KEY_RANGE, PRED_VALUE_RANGE, PRED_KEY_MASK, PRED_BLOCK_BOX = 0, 1, 2, 3, 4
+PRED_ALL, PRED_KEY_RANGE, PRED_VALUE_RANGE, PRED_KEY_MASK, PRED_BLOCK_BOX, PRED_SHORT3_BOX = 0, 1, 2, 3, 4, 5
 # ops, hash modes
 OP_INSERT, OP_FIND, OP_ERASE = 0, 1, 2
-HASH_MIX64, HASH_TESCHNER = 0, 1
+HASH_MIX64, HASH_TESCHNER, HASH_TESCHNER_SHORT3 = 0, 1, 2
 
 EXPORTS = [
     "hc_abi_version", "hc_last_error", "hc_table_bytes", "hc_create", "hc_destroy", "hc_set_launch",
@@ -33,6 +33,7 @@ EXPORTS = [
     "hc_batch_launch", "hc_batch_destroy", "hc_batch_run_noalloc", "hc_measure_random_reads",
     "hc_batch_scratch_bytes", "hc_batch_run", "hc_device_view_get", "hc_select",
     "hc_ordered_scratch_bytes", "hc_insert_ordered", "hc_erase_ordered", "hc_apply_mixed",
+    "hc_pack_short3", "hc_unpack_short3",
 ]
 
 
@@ -122,6 +123,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_insert_ordered": (i32, [vp, vp, vp, i64, vp, vp, i64, vp]),
         "hc_erase_ordered": (i32, [vp, vp, i64, vp, vp, i64, vp]),
         "hc_apply_mixed": (i32, [vp, vp, vp, vp, i64, vp, vp, vp]),
+        "hc_pack_short3": (i32, [vp, i64, vp, vp]),
+        "hc_unpack_short3": (i32, [vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

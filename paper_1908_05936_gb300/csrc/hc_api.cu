@@ -77,9 +77,9 @@ hc_rc check_config(int kind, const hc_config *cfg, int *bb, int *hash_mode, unsi
         *seed = cfg->seed;
     }
     if (*bb != 32 && *bb != 64 && *bb != 128) return fail(HC_ERR_ARG, "bucket_bytes must be 32, 64 or 128 (got %d)", *bb);
-    if (*hash_mode != HC_HASH_MIX64 && *hash_mode != HC_HASH_TESCHNER)
+    if (*hash_mode != HC_HASH_MIX64 && *hash_mode != HC_HASH_TESCHNER && *hash_mode != HC_HASH_TESCHNER_SHORT3)
         return fail(HC_ERR_ARG, "unknown hash_mode %d", *hash_mode);
-    if (*hash_mode == HC_HASH_TESCHNER && kind != HC_MAP_I64_I32)
+    if (*hash_mode != HC_HASH_MIX64 && kind != HC_MAP_I64_I32)
         return fail(HC_ERR_ARG, "the spatial hash applies to packed int64 block keys (HC_MAP_I64_I32) only");
     return HC_OK;
 }
@@ -595,13 +595,13 @@ hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, void *d
     if (!d_count) return fail(HC_ERR_ARG, "d_count is NULL");
     if ((rc = check_array(d_count, 8, "d_count")) != HC_OK) return rc;
     if (cap < 0) return fail(HC_ERR_ARG, "cap must be >= 0");
-    if (pred->kind < HC_PRED_ALL || pred->kind > HC_PRED_BLOCK_BOX)
+    if (pred->kind < HC_PRED_ALL || pred->kind > HC_PRED_SHORT3_BOX)
         return fail(HC_ERR_ARG, "unknown predicate kind %d", pred->kind);
     if (pred->negate != 0 && pred->negate != 1) return fail(HC_ERR_ARG, "negate must be 0 or 1");
     if (pred->kind == HC_PRED_VALUE_RANGE && !is_map(t->kind))
         return fail(HC_ERR_ARG, "HC_PRED_VALUE_RANGE needs a map");
-    if (pred->kind == HC_PRED_BLOCK_BOX && t->kind == HC_SET_U32)
-        return fail(HC_ERR_ARG, "HC_PRED_BLOCK_BOX needs 64-bit keys");
+    if ((pred->kind == HC_PRED_BLOCK_BOX || pred->kind == HC_PRED_SHORT3_BOX) && t->kind == HC_SET_U32)
+        return fail(HC_ERR_ARG, "a box predicate needs 64-bit keys");
     if (cap > 0 && (rc = check_array(d_keys_out, key_bytes(t->kind), "keys output")) != HC_OK) return rc;
     if (cap > 0 && d_vals_out && is_map(t->kind) &&
         (rc = check_array(d_vals_out, val_bytes(t->kind), "values output")) != HC_OK)
@@ -649,6 +649,34 @@ static void fill_view(const hc_table *t, hc_device_view *out) {
     out->bucket_bytes = t->bucket_bytes;
     out->hash_mode = t->view.hash_mode;
     out->pad_from = t->view.pad_from;
+}
+
+hc_rc hc_pack_short3(const int16_t *d_xyz, int64_t n, int64_t *d_keys, void *stream) {
+    if (n < 0) return fail(HC_ERR_ARG, "n must be >= 0 (got %lld)", (long long)n);
+    if (n == 0) return HC_OK;
+    hc_rc rc;
+    if ((rc = check_array(d_xyz, 2, "short3 array")) != HC_OK) return rc;
+    if ((rc = check_array(d_keys, 8, "keys")) != HC_OK) return rc;
+    int dev = 0;
+    HC_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    HC_CUDA(hc::pack_short3(d_xyz, n, reinterpret_cast<long long *>(d_keys), sm_count_of(dev),
+                            static_cast<cudaStream_t>(stream)),
+            "launching the short3 packing kernel");
+    return HC_OK;
+}
+
+hc_rc hc_unpack_short3(const int64_t *d_keys, int64_t n, int16_t *d_xyz, void *stream) {
+    if (n < 0) return fail(HC_ERR_ARG, "n must be >= 0 (got %lld)", (long long)n);
+    if (n == 0) return HC_OK;
+    hc_rc rc;
+    if ((rc = check_array(d_keys, 8, "keys")) != HC_OK) return rc;
+    if ((rc = check_array(d_xyz, 2, "short3 array")) != HC_OK) return rc;
+    int dev = 0;
+    HC_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    HC_CUDA(hc::unpack_short3(reinterpret_cast<const long long *>(d_keys), n, d_xyz, sm_count_of(dev),
+                              static_cast<cudaStream_t>(stream)),
+            "launching the short3 unpacking kernel");
+    return HC_OK;
 }
 
 hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream) {

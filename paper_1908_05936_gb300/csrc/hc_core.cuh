@@ -52,7 +52,7 @@ namespace hc {
 enum : int { KIND_SET_U32 = 0, KIND_SET_U64 = 1, KIND_MAP_I64_I32 = 2, KIND_MAP_U64_U64 = 3 };
 enum : uint32_t { ST_INSERTED = 0, ST_EXISTS = 1, ST_OVERFLOW = 2, ST_ERASED = 3, ST_NOT_FOUND = 4 };
 enum : uint32_t { ERR_OVERFLOW = 1u, ERR_PROBE_BOUND = 2u };
-enum : int { HASH_MIX64 = 0, HASH_TESCHNER = 1 };
+enum : int { HASH_MIX64 = 0, HASH_TESCHNER = 1, HASH_TESCHNER_SHORT3 = 2 };
 
 // Restarts of an insert probe after lost compare-and-swap races.  Each lost
 // race means another key took a slot, so a correct table never reaches this
@@ -136,8 +136,18 @@ __device__ __forceinline__ unsigned long long teschner(unsigned long long key) {
     return (x * 73856093ull) ^ (y * 19349669ull) ^ (z * 83492791ull);
 }
 
+// The same hash on the paper's own key type, a short3 of signed 16-bit
+// coordinates packed as (uint16)x | (uint16)y << 16 | (uint16)z << 32.
+__device__ __forceinline__ unsigned long long teschner_short3(unsigned long long key) {
+    const unsigned long long x = (unsigned long long)(long long)(short)(key & 0xFFFFull);
+    const unsigned long long y = (unsigned long long)(long long)(short)((key >> 16) & 0xFFFFull);
+    const unsigned long long z = (unsigned long long)(long long)(short)((key >> 32) & 0xFFFFull);
+    return (x * 73856093ull) ^ (y * 19349669ull) ^ (z * 83492791ull);
+}
+
 __device__ __forceinline__ unsigned long long first_bucket(const View &v, unsigned long long key) {
     if (v.hash_mode == HASH_TESCHNER) return teschner(key) % v.nb;
+    if (v.hash_mode == HASH_TESCHNER_SHORT3) return teschner_short3(key) % v.nb;
     return __umul64hi(fmix64(key ^ v.seed), v.nb);
 }
 

@@ -57,6 +57,10 @@ const uint8_t *ordered_skip(long long n, const void *scratch);
 cudaError_t mixed_ops(const hc_device_view &dv, const uint8_t *ops, const void *keys, const void *vals, long long n,
                       uint8_t *status, void *vals_out, cudaStream_t s);
 
+// short3 keys <-> packed int64 keys (hc_select.cu).
+cudaError_t pack_short3(const int16_t *xyz, long long n, long long *keys, int sms, cudaStream_t s);
+cudaError_t unpack_short3(const long long *keys, long long n, int16_t *xyz, int sms, cudaStream_t s);
+
 // Appends the stored entries of the table behind dv that satisfy p (hc_select).
 cudaError_t select_entries(const hc_device_view &dv, const SelectPred &p, void *ko, void *vo, unsigned long long cap,
                            unsigned long long *count, unsigned long long positions, int sms, cudaStream_t s);

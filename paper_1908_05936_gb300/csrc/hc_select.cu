@@ -43,6 +43,13 @@ struct Selector {
                 r = x >= p.box[0] && x <= p.box[1] && y >= p.box[2] && y <= p.box[3] && z >= p.box[4] && z <= p.box[5];
                 break;
             }
+            case HC_PRED_SHORT3_BOX: {
+                const long long x = (short)((unsigned long long)k & 0xFFFFull);
+                const long long y = (short)(((unsigned long long)k >> 16) & 0xFFFFull);
+                const long long z = (short)(((unsigned long long)k >> 32) & 0xFFFFull);
+                r = x >= p.box[0] && x <= p.box[1] && y >= p.box[2] && y <= p.box[3] && z >= p.box[4] && z <= p.box[5];
+                break;
+            }
             default: break;   // HC_PRED_ALL
         }
         return r != (p.negate != 0);
@@ -70,6 +77,43 @@ cudaError_t launch(const hc_device_view &dv, const SelectPred &p, void *ko, void
 }
 
 }  // namespace
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_pack_short3(const int16_t *xyz, long long n, long long *keys) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long x = (uint16_t)xyz[3 * i], y = (uint16_t)xyz[3 * i + 1], z = (uint16_t)xyz[3 * i + 2];
+        keys[i] = (long long)(x | (y << 16) | (z << 32));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_unpack_short3(const long long *keys, long long n, int16_t *xyz) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long k = (unsigned long long)keys[i];
+        xyz[3 * i] = (int16_t)(k & 0xFFFFull);
+        xyz[3 * i + 1] = (int16_t)((k >> 16) & 0xFFFFull);
+        xyz[3 * i + 2] = (int16_t)((k >> 32) & 0xFFFFull);
+    }
+}
+
+unsigned grid_for_items(long long n, int sms) {
+    const long long g = (n + 255) / 256;
+    return (unsigned)std::max<long long>(1, std::min<long long>(g, (long long)sms * 8));
+}
+
+}  // namespace
+
+cudaError_t pack_short3(const int16_t *xyz, long long n, long long *keys, int sms, cudaStream_t s) {
+    k_pack_short3<<<grid_for_items(n, sms), 256, 0, s>>>(xyz, n, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t unpack_short3(const long long *keys, long long n, int16_t *xyz, int sms, cudaStream_t s) {
+    k_unpack_short3<<<grid_for_items(n, sms), 256, 0, s>>>(keys, n, xyz);
+    return cudaGetLastError();
+}
 
 cudaError_t select_entries(const hc_device_view &dv, const SelectPred &p, void *ko, void *vo, unsigned long long cap,
                            unsigned long long *count, unsigned long long positions, int sms, cudaStream_t s) {

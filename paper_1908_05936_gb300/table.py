@@ -52,6 +52,25 @@ def _check_tensor(t: torch.Tensor, nbytes: int, name: str):
         raise TypeError(f"{name} must be contiguous with {nbytes}-byte elements")
 
 
+def pack_short3(xyz: torch.Tensor, stream=None) -> torch.Tensor:
+    """(n, 3) int16 CUDA tensor of block coordinates -> n packed int64 keys
+    (hc_pack_short3) for a map created with HASH_TESCHNER_SHORT3."""
+    if not isinstance(xyz, torch.Tensor) or not xyz.is_cuda or xyz.dtype != torch.int16 or not xyz.is_contiguous():
+        raise TypeError("xyz must be a contiguous int16 CUDA tensor of shape (n, 3)")
+    n = xyz.numel() // 3
+    keys = torch.empty(n, dtype=torch.int64, device=xyz.device)
+    L.check(L.load().hc_pack_short3(xyz.data_ptr(), n, keys.data_ptr(), _stream_handle(stream)))
+    return keys
+
+
+def unpack_short3(keys: torch.Tensor, stream=None) -> torch.Tensor:
+    """Packed int64 keys -> (n, 3) int16 coordinates (hc_unpack_short3)."""
+    _check_tensor(keys, 8, "keys")
+    xyz = torch.empty((keys.numel(), 3), dtype=torch.int16, device=keys.device)
+    L.check(L.load().hc_unpack_short3(keys.data_ptr(), keys.numel(), xyz.data_ptr(), _stream_handle(stream)))
+    return xyz
+
+
 class Table:
     """A fixed-capacity GPU hash set or map (``kind`` in L.SET_U32 .. L.MAP_U64_U64)."""
 

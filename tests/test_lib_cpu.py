@@ -56,6 +56,12 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.hc_insert_ordered(None, None, None, 1, None, None, 0, None) == L.ERR_ARG
     assert lib.hc_erase_ordered(None, None, 1, None, None, 0, None) == L.ERR_ARG
     assert lib.hc_apply_mixed(None, None, None, None, 1, None, None, None) == L.ERR_ARG
+    assert lib.hc_pack_short3(None, -1, None, None) == L.ERR_ARG
+    assert lib.hc_pack_short3(None, 0, None, None) == L.OK
+    assert lib.hc_unpack_short3(None, 1, None, None) == L.ERR_ARG
+    s3 = L.Config(32, L.HASH_TESCHNER_SHORT3, 0)
+    assert lib.hc_create(ctypes.byref(h), L.SET_U64, 16, ctypes.byref(s3), None) == L.ERR_ARG
+    assert lib.hc_create(ctypes.byref(h), L.MAP_I64_I32, 16, ctypes.byref(L.Config(32, 3, 0)), None) == L.ERR_ARG
     pred = L.Predicate(L.PRED_ALL, 0, 0, 0)
     assert lib.hc_select(None, ctypes.byref(pred), None, None, 0, None, None) == L.ERR_ARG
     assert lib.hc_batch_destroy(None) == L.OK

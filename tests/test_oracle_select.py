@@ -92,3 +92,20 @@ def test_value_range_signed_int32():
         assert k.tolist() == [3, 4, 5, 6] and v.tolist() == [-2, -1, 0, 1]
     finally:
         t.close()
+
+
+def test_short3_box_equals_enumerated_coordinates():
+    """Packed short3 keys (16-bit fields) built from coordinates near both
+    ends of the int16 range: the box selects exactly the enumerated ones."""
+    vals = [-32768, -32767, -2, -1, 0, 1, 32766, 32767]
+    coords = list(itertools.product(vals, repeat=3))
+    keys = [(x & 0xFFFF) | ((y & 0xFFFF) << 16) | ((z & 0xFFFF) << 32) for x, y, z in coords]
+    t = _table(O.MAP_I64_I32, keys, list(range(len(keys))))
+    try:
+        for b in ((-32768, -1, -2, 1, 0, 32767), (-1, 1, -32767, 32766, -32768, -32768)):
+            expected = sorted(k for k, (x, y, z) in zip(keys, coords)
+                              if b[0] <= x <= b[1] and b[2] <= y <= b[3] and b[4] <= z <= b[5])
+            k, _ = t.select(O.PRED_SHORT3_BOX, box=b)
+            assert sorted(k.tolist()) == expected and len(expected) > 0
+    finally:
+        t.close()
