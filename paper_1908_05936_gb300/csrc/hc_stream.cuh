@@ -21,7 +21,37 @@
 #define HC_STREAM_ERASE_MINB 1
 #endif
 
+// Lookups read buckets through L1 (the read-only path) when 1: a lookup
+// never runs together with a modifying call on its table, so the line a
+// probe brings into L1 is still valid when a matching key's value is read
+// from it right after.  0: L2 only, as the modifying kernels read.
+#ifndef HC_FIND_L1
+#define HC_FIND_L1 0
+#endif
+
 namespace hc {
+
+template <int LB>
+__device__ __forceinline__ void load_find(LaneWords<LB> &lw, const unsigned char *p) {
+    if constexpr (HC_FIND_L1 && LB >= 32) {
+#pragma unroll
+        for (int q = 0; q < LB / 32; ++q)
+            asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(lw.w[4 * q]), "=l"(lw.w[4 * q + 1]), "=l"(lw.w[4 * q + 2]), "=l"(lw.w[4 * q + 3])
+                         : "l"(p + 32 * q));
+    } else {
+        lw.load(p);
+    }
+}
+
+template <int KIND, int BB>
+__device__ __forceinline__ unsigned long long load_find_val(const View &v, unsigned long long b, int s) {
+    using T = Traits<KIND>;
+    if constexpr (HC_FIND_L1 && T::MAP)
+        return (unsigned long long)__ldg(reinterpret_cast<const typename T::Val *>(Slots<KIND, BB>::val(v, b, s)));
+    else
+        return load_val<KIND, BB>(v, b, s);
+}
 
 template <int KIND, int BB, int KPT, int S>
 __global__ void __launch_bounds__(256, HC_STREAM_FIND_MINB)
@@ -78,7 +108,7 @@ k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8
         LaneWords<LB> lw[S];
 #pragma unroll
         for (int s = 0; s < S; ++s)
-            if (active >> s & 1u) lw[s].load(v.buckets + b[s] * BB);
+            if (active >> s & 1u) load_find<LB>(lw[s], v.buckets + b[s] * BB);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             if (!(active >> s & 1u)) continue;
@@ -92,7 +122,7 @@ k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8
             bool done = false;
             if (lm) {
                 sf[idx[s]] = 1;
-                if constexpr (T::MAP) sv[idx[s]] = (Val)load_val<KIND, BB>(v, b[s], __ffs(lm) - 1);
+                if constexpr (T::MAP) sv[idx[s]] = (Val)load_find_val<KIND, BB>(v, b[s], __ffs(lm) - 1);
                 done = true;
             } else if (le || ++probes[s] >= v.nb) {
                 sf[idx[s]] = 0;
