@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--lane-bytes", type=int, default=0)
     ap.add_argument("--kpt", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--find-lane-bytes", type=int, default=0,
+                    help="lane bytes of the lookups only (the bucket size: lane-pair lookups for maps)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=24)
@@ -206,6 +208,8 @@ def run_gpu(args, rank: int, world: int):
     t = Table(L.MAP_U64_U64, wl.slots, bucket_bytes=bb)
     for op in (0, 1, 2):
         t.set_launch(op, lane_bytes=args.lane_bytes, keys_per_group=args.kpt, block=args.block)
+    if args.find_lane_bytes:
+        t.set_launch(1, lane_bytes=args.find_lane_bytes)
     stream = torch.cuda.current_stream()
     calls = []   # (name, n, start_event, end_event)
     in_kernel = args.workload == "device_api"

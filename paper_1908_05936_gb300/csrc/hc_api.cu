@@ -355,9 +355,11 @@ hc_rc hc_set_launch(hc_table *t, int32_t op, const hc_launch *shape) {
                     "lane_bytes must be 32, 64 or 128 (16 for maps) and at most the %d-byte key region, or the whole "
                     "bucket for maps", krb);
     if (sh.keys_per_group != 1 && sh.keys_per_group != 2 &&
-        !((sh.keys_per_group == 4 || sh.keys_per_group == 8) && sh.lane_bytes == krb))
+        !((sh.keys_per_group == 4 || sh.keys_per_group == 8) &&
+          (sh.lane_bytes == krb || (op == hc::OP_FIND && is_map(t->kind) && sh.lane_bytes == t->bucket_bytes &&
+                                    2 * krb == t->bucket_bytes))))
         return fail(HC_ERR_ARG,
-                    "keys_per_group must be 1 or 2 (4 or 8: streaming, lane = the key region)");
+                    "keys_per_group must be 1 or 2 (4 or 8: streaming, lane = the key region, or the whole bucket for map lookups)");
     if (sh.block < 64 || sh.block > 256 || sh.block % 32)
         return fail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     t->shape[op] = sh;

@@ -190,6 +190,18 @@ cudaError_t launch_find_stream(const View &v, const void *keys, long long n, uin
 }
 
 template <int KIND, int BB, int KPT, int S>
+cudaError_t launch_find_pair(const View &v, const void *keys, long long n, uint8_t *out, void *vals_out, int block,
+                             cudaStream_t s) {
+    using T = Traits<KIND>;
+    const long long chunk = (long long)(block / 2) * KPT;
+    const unsigned grid = (unsigned)((n + chunk - 1) / chunk);
+    const size_t smem = (size_t)chunk * (sizeof(typename T::Key) + sizeof(typename T::Val) + 1);
+    k_find_pair<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys, n, out,
+                                                            (typename T::Val *)vals_out);
+    return cudaGetLastError();
+}
+
+template <int KIND, int BB, int KPT, int S>
 cudaError_t launch_insert_stream(const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
                                  const uint8_t *skip, int block, cudaStream_t s) {
     using T = Traits<KIND>;
@@ -215,7 +227,15 @@ cudaError_t launch_erase_stream(const View &v, const void *keys, long long n, ui
 template <int KIND, int BB, int LB>
 cudaError_t launch_range_kpt(int op, const View &v, const void *keys, const void *vals, long long n, uint8_t *out,
                              void *vals_out, const LaunchShape &sh, const uint8_t *skip, cudaStream_t s) {
-    if (sh.keys_per_group >= 4) {       // streaming forms: one thread per key
+    if (sh.keys_per_group >= 4) {       // streaming forms: one thread per key, or a lane pair per map key
+        if constexpr (Traits<KIND>::MAP && LB == BB && Slots<KIND, BB>::KRB * 2 == BB) {
+            if (n <= 0) return cudaSuccess;
+            if (op == OP_FIND) {
+                if (sh.keys_per_group == 4) return launch_find_pair<KIND, BB, 4, 2>(v, keys, n, out, vals_out, sh.block, s);
+                if (sh.keys_per_group == 8) return launch_find_pair<KIND, BB, 8, 4>(v, keys, n, out, vals_out, sh.block, s);
+            }
+            return cudaErrorInvalidValue;
+        }
         if constexpr (LB == Slots<KIND, BB>::KRB) {
             if (n <= 0) return cudaSuccess;
             if (op == OP_FIND) {

@@ -146,6 +146,154 @@ k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8
     }
 }
 
+// Streaming map lookup by lane pairs: the two lanes of a pair handle one key.
+// The first probe reads the key's first bucket in one instruction, the even
+// lane its key region (the first BB/2 bytes), the odd lane its values (the
+// rest): one request for one line, and a match there (most present keys) has
+// its value without a second, dependent request.  Later probes read the key
+// regions of two consecutive buckets at once (even lane: b, odd lane: b + 1),
+// so a probe chain advances two buckets per round; a match found there reads
+// its value separately.  The pair keeps identical state and control flow and
+// exchanges the comparison masks with shuffles.
+template <int KIND, int BB, int KPT, int S>
+__global__ void __launch_bounds__(256, HC_STREAM_FIND_MINB)
+k_find_pair(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *found,
+            typename Traits<KIND>::Val *vals_out) {
+    using T = Traits<KIND>;
+    using Key = typename T::Key;
+    using Val = typename T::Val;
+    using Sl = Slots<KIND, BB>;
+    constexpr int HB = BB / 2;                    // bytes per lane
+    constexpr int SPL = Sl::SPB;
+    static_assert(T::MAP && Sl::KRB == HB, "a pair splits a map bucket into keys and values");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int pairs = blockDim.x / 2;
+    const int chunk = pairs * KPT;
+    Key *sk = reinterpret_cast<Key *>(smem);
+    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * sizeof(Key));
+    uint8_t *sf = smem + (size_t)chunk * (sizeof(Key) + sizeof(Val));
+
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sk[i] = ld_stream(keys + c0 + i);
+    __syncthreads();
+
+    const unsigned lane = threadIdx.x & 31;
+    const bool odd = lane & 1u;
+    const unsigned pmask = 3u << (lane & 30u);
+    const int pair = threadIdx.x >> 1;
+    int idx[S];
+    Key key[S];
+    unsigned long long b[S];
+    uint32_t probes[S];
+    bool first[S];
+    int next = 0;
+    uint32_t active = 0;
+    auto take = [&](int s) {
+        while (next < KPT) {
+            const int i = pair + (next++) * pairs;
+            if (i >= m) { next = KPT; break; }
+            const Key k = sk[i];
+            const int side = side_index<KIND>(k);
+            if (side >= 0) {
+                if (!odd) {
+                    const uint32_t pres = *((volatile unsigned int *)&v.hdr->side_present[side]);
+                    sf[i] = pres ? 1 : 0;
+                    sv[i] = pres ? (Val) * ((volatile unsigned long long *)&v.hdr->side_val[side]) : (Val)0;
+                }
+                continue;
+            }
+            idx[s] = i;
+            key[s] = k;
+            b[s] = first_bucket(v, (unsigned long long)k);
+            probes[s] = 0;
+            first[s] = true;
+            active |= 1u << s;
+            return;
+        }
+    };
+#pragma unroll
+    for (int s = 0; s < S; ++s) take(s);
+    while (active) {
+        LaneWords<HB> lw[S];
+        // first probe of a key: keys (even lane) and values (odd lane) of its
+        // first bucket; later probes: the key regions of two buckets, b (even
+        // lane) and the next one (odd lane)
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!(active >> s & 1u)) continue;
+            const unsigned long long bb = (odd && !first[s]) ? next_bucket(v, b[s]) : b[s];
+            load_find<HB>(lw[s], v.buckets + bb * BB + ((odd && first[s]) ? HB : 0));
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!(active >> s & 1u)) continue;
+            uint32_t lm = 0, le = 0;
+            if (!odd || !first[s]) {
+#pragma unroll
+                for (int q = 0; q < SPL; ++q) {
+                    const Key ks = slot_key<KIND, HB>(lw[s], q);
+                    lm |= (uint32_t)(ks == key[s]) << q;
+                    le |= (uint32_t)(ks == T::EMPTY) << q;
+                }
+            }
+            const uint32_t lm0 = __shfl_sync(pmask, lm, lane & 30u), le0 = __shfl_sync(pmask, le, lane & 30u);
+            const uint32_t lm1 = __shfl_sync(pmask, lm, lane | 1u), le1 = __shfl_sync(pmask, le, lane | 1u);
+            int hit = -1;                      // bucket offset (0 or 1) of a match
+            bool absent = false;
+            if (first[s]) {
+                if (lm0) {
+                    const int q = __ffs(lm0) - 1;
+                    if (odd) {
+                        Val val = 0;           // select the word without indexing registers at run time
+#pragma unroll
+                        for (int qq = 0; qq < SPL; ++qq) {
+                            if constexpr (sizeof(Val) == 8) {
+                                if (qq == q) val = (Val)lw[s].w[qq];
+                            } else {
+                                if (qq == q) val = (Val)(uint32_t)(lw[s].w[qq >> 1] >> ((qq & 1) * 32));
+                            }
+                        }
+                        sv[idx[s]] = val;
+                    } else {
+                        sf[idx[s]] = 1;
+                    }
+                    hit = 2;                   // resolved with its value
+                } else if (le0 || ++probes[s] >= v.nb) {
+                    absent = true;
+                } else {
+                    b[s] = next_bucket(v, b[s]);
+                    first[s] = false;
+                }
+            } else {
+                if (lm0) hit = 0;
+                else if (le0 || ++probes[s] >= v.nb) absent = true;
+                else if (lm1) hit = 1;
+                else if (le1 || ++probes[s] >= v.nb) absent = true;
+                else b[s] = next_bucket(v, next_bucket(v, b[s]));
+                if (hit >= 0 && !odd) {        // a later bucket: the value needs its own read
+                    const unsigned long long hb = hit ? next_bucket(v, b[s]) : b[s];
+                    sf[idx[s]] = 1;
+                    sv[idx[s]] = (Val)load_find_val<KIND, BB>(v, hb, __ffs(hit ? lm1 : lm0) - 1);
+                }
+            }
+            if (absent && !odd) {
+                sf[idx[s]] = 0;
+                sv[idx[s]] = (Val)0;
+            }
+            if (hit >= 0 || absent) {
+                active &= ~(1u << s);
+                take(s);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        if (found) st_stream(found + c0 + i, sf[i]);
+        if (vals_out) st_stream(vals_out + c0 + i, sv[i]);
+    }
+}
+
 // Streaming insert: the same staging and refilling as k_find_stream.  Within
 // one round every slot first decides whether it claims, then all claiming
 // slots issue their compare-and-swap together, so the atomics of different

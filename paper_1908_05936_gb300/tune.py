@@ -7,7 +7,9 @@ GPU.  Results never depend on the shape; only speed does.
 For each (kind, bucket bytes) it fills a table to load factor 0.8 in batches
 of 2^(slots_log2 - 2) keys, then times every candidate shape on insert (the
 last batch of the fill), find (all present), find (all absent) and erase
-with CUDA events, and keeps the fastest shape per operation.  The winners are
+with CUDA events, and keeps the fastest shape per operation; "find" is the
+shape with the least time for the present and the absent batch together,
+the one `apply()` installs.  The winners are
 written to a JSON cache keyed by device name and SM count
 (`tuned.json` next to this file); `apply()` installs them on a table.
 """
@@ -83,6 +85,10 @@ def candidates(table: Table) -> list[dict]:
     out = [dict(lane_bytes=lb, keys_per_group=k, block=b) for lb in lanes for k in KEYS_IN_FLIGHT for b in BLOCKS]
     # streaming forms: one thread per key over the key region, probes refilled as they finish
     out += [dict(lane_bytes=krb, keys_per_group=k, block=b) for k in (4, 8) for b in BLOCKS]
+    # map lookups by lane pairs (one lane the keys, its partner the values)
+    if table.is_map and 2 * krb == table.bucket_bytes:
+        out += [dict(lane_bytes=table.bucket_bytes, keys_per_group=k, block=b, find_only=True) for k in (4, 8)
+                for b in BLOCKS]
     return out
 
 
@@ -99,7 +105,10 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
         t.insert(fill[off:off + batch], vals[off:off + batch] if vals is not None else None, status=False)
     last = fill[n_fill - batch:]
     last_v = vals[n_fill - batch:] if vals is not None else None
-    hit = fill[:batch]
+    # present keys sampled from the whole fill (keys inserted early sit in
+    # their first bucket more often than keys inserted at a high load factor)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    hit = fill[torch.randperm(n_fill, device="cuda", generator=gen)[:batch]]
     miss = _keys(kind, 4, 0, batch)
     out = torch.empty(batch, dtype=torch.uint8, device="cuda")
     vout = torch.empty(batch, dtype=torch.int32 if kind == L.MAP_I64_I32 else torch.int64, device="cuda") \
@@ -107,7 +116,8 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
     results = {"insert": [], "find_hit": [], "find_miss": [], "erase": []}
     t.insert(last, last_v, status=False)                  # the table starts at the target load factor
     for c in candidates(t):
-        for op in (L.OP_INSERT, L.OP_FIND, L.OP_ERASE):
+        find_only = c.pop("find_only", False)
+        for op in ((L.OP_FIND,) if find_only else (L.OP_INSERT, L.OP_FIND, L.OP_ERASE)):
             t.set_launch(op, fold=2, **c)
 
         def ins():
@@ -118,12 +128,16 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
 
         # erase / re-insert the last batch: each insert stores new keys into a
         # table at the target load factor, each erase removes present keys
-        e_ms, i_ms = [], []
-        for _ in range(2):
-            e_ms.append(_time_once(era))
-            i_ms.append(_time_once(ins))
-        results["insert"].append((min(i_ms), c))
-        results["erase"].append((min(e_ms), c))
+        if find_only:
+            results["insert"].append((float("inf"), c))
+            results["erase"].append((float("inf"), c))
+        else:
+            e_ms, i_ms = [], []
+            for _ in range(2):
+                e_ms.append(_time_once(era))
+                i_ms.append(_time_once(ins))
+            results["insert"].append((min(i_ms), c))
+            results["erase"].append((min(e_ms), c))
         results["find_hit"].append((_time(lambda: t.find(hit, found=out, vals_out=vout)), c))
         results["find_miss"].append((_time(lambda: t.find(miss, found=out, vals_out=vout)), c))
     t.close()
@@ -131,12 +145,16 @@ def tune_table(kind: int, bucket_bytes: int, slots_log2: int = 26, lf: float = 0
         for i, (_, c) in enumerate(results["find_hit"]):
             row = dict(c, bucket_bytes=bucket_bytes, kind=kind)
             for op, lst in results.items():
-                row[op + "_mops"] = round(batch / lst[i][0] / 1e3, 1)
+                row[op + "_mops"] = round(batch / lst[i][0] / 1e3, 1) if lst[i][0] != float("inf") else None
             every.append(row)
     best = {}
     for op, lst in results.items():
         ms, c = min(lst, key=lambda x: x[0])
         best[op] = dict(c, ms=round(ms, 4), mops=round(batch / ms / 1e3, 1))
+    # lookups of a mix of present and absent keys: the least total time
+    both = [(h[0] + m[0], h[1]) for h, m in zip(results["find_hit"], results["find_miss"])]
+    ms, c = min(both, key=lambda x: x[0])
+    best["find"] = dict(c, ms=round(ms, 4), mops=round(2 * batch / ms / 1e3, 1))
     return best
 
 
@@ -170,7 +188,8 @@ def apply(table: Table) -> bool:
     best = cache.get(f"{name}/{table.bucket_bytes}")
     if not best:
         return False
-    for op, key in ((L.OP_INSERT, "insert"), (L.OP_FIND, "find_hit"), (L.OP_ERASE, "erase")):
+    for op, key in ((L.OP_INSERT, "insert"), (L.OP_FIND, "find" if "find" in best else "find_hit"),
+                    (L.OP_ERASE, "erase")):
         b = best[key]
         table.set_launch(op, lane_bytes=b["lane_bytes"], keys_per_group=b["keys_per_group"], block=b["block"])
     return True

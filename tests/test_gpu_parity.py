@@ -264,14 +264,18 @@ def test_host_buffer_calls(kind):
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("bb", (32, 64, 128))
 @pytest.mark.parametrize("kpt", (4, 8))
-def test_streaming_find(kind, bb, kpt):
+@pytest.mark.parametrize("pair", (False, True))
+def test_streaming_find(kind, bb, kpt, pair):
     """Streaming lookup (keys staged per block, several probes in flight per
     thread, refilled as they finish) against the oracle, with side-slot keys,
-    duplicates, ragged chunk tails, absent and erased keys."""
+    duplicates, ragged chunk tails, absent and erased keys; for maps also by
+    lane pairs (one lane reads the keys, its partner the values)."""
+    if pair and kind not in (O.MAP_I64_I32, O.MAP_U64_U64):
+        pytest.skip("lane pairs split map buckets")
     rng = np.random.default_rng(bb + kpt + kind)
     p = Pair(kind, 20000, bucket_bytes=bb)
     krb = p.g.get_launch(0)["lane_bytes"]
-    p.g.set_launch(1, lane_bytes=krb, keys_per_group=kpt, block=96)
+    p.g.set_launch(1, lane_bytes=bb if pair else krb, keys_per_group=kpt, block=96)
     try:
         keys = random_keys(kind, 15000, rng)
         keys = np.concatenate([keys, np.array(RESERVED[kind])])
