@@ -457,6 +457,70 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
 HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg,
                                   void *stream);
 
+/* ---- served form: a continuous-batching request loop ---------------------
+ * Not in the paper (which has one container per call); it serves the range
+ * calls of Section 4.1 to a stream of requests over resident tables.  A
+ * request is one insert / find / erase of a host key array on one table.
+ * The loop, run on the calling host thread:
+ *   1. an arrived request joins its table's FIFO; a table belongs to one lane
+ *      (a CUDA stream, table index mod lanes), so its requests reach the GPU
+ *      in arrival order;
+ *   2. each lane owns `depth` launch slots; a slot is a device staging buffer
+ *      of slot_bytes (keys, values, results) with pinned host staging of the
+ *      same size and descriptor scratch -- the slots and the resident tables
+ *      are the whole HBM budget;
+ *   3. a free slot takes the heads of its lane's FIFOs, one per table, while
+ *      they fit (at most max_items), copies their inputs host->device (small
+ *      requests packed into one copy), runs one hc_batch_run over them
+ *      (merge = 1) or one range call each (merge = 0), copies the results
+ *      device->host and records an event;
+ *   4. a finished slot hands each request its results and completion time.
+ * Requests wait for a slot; none is dropped.  A request bigger than a slot is
+ * HC_ERR_ARG before anything runs. */
+typedef struct hc_server hc_server;
+
+typedef struct hc_serve_config {
+    int32_t lanes;           /* streams (default 4)                              */
+    int32_t depth;           /* launch slots per lane (default 2)                */
+    int64_t slot_bytes;      /* device (and pinned host) bytes per slot (default 64 MiB) */
+    int32_t merge;           /* 1: one batched launch per slot; 0: one call per request */
+    int32_t max_items;       /* requests per merged launch (default 256, at most 4096) */
+    hc_batch_config batch;   /* shape of the merged launches (use_graph must be 0) */
+} hc_serve_config;
+
+typedef struct hc_request {
+    int32_t table;           /* index into the server's tables                  */
+    int32_t op;              /* HC_OP_*                                          */
+    const void *h_keys;      /* host keys (pinned memory copies asynchronously)  */
+    const void *h_vals;      /* host values of a map insert, else NULL           */
+    int64_t n;               /* keys                                            */
+    uint8_t *h_status;       /* host output: insert/erase status or found flags  */
+    void *h_vals_out;        /* host output: values of a map find, may be NULL   */
+    double arrival;          /* seconds after the run starts                     */
+    double done;             /* written: seconds after the start when the host
+                                holds the results                                */
+} hc_request;
+
+typedef struct hc_serve_stats {
+    int64_t requests, ops, launches, queued_max;
+    double wall_s;
+    double p50_ms, p99_ms, p999_ms, max_ms;   /* latency: arrival (0 when not
+                                                 realtime) to done            */
+} hc_serve_stats;
+
+/* tables: n_tables handles on the current device; the server keeps the
+ * pointers (the tables must outlive it).  Allocates the slots. */
+HC_API hc_rc hc_server_create(hc_server **out, hc_table *const *tables, int32_t n_tables, const hc_serve_config *cfg);
+/* Serve `reqs` (sorted by arrival).  realtime = 1 admits a request when its
+ * arrival time has passed; 0 treats every request as arrived at the start (a
+ * capacity run).  Synchronises the device first (work queued on any stream
+ * before the run comes first).  Returns when every request is done
+ * (HC_ERR_STATE after timeout_s seconds).  Fills each request's outputs and
+ * `done`, and *stats (may be NULL). */
+HC_API hc_rc hc_server_run(hc_server *srv, hc_request *reqs, int64_t n_reqs, int32_t realtime, double timeout_s,
+                           hc_serve_stats *stats);
+HC_API hc_rc hc_server_destroy(hc_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ EXPORTS = [
     "hc_batch_launch", "hc_batch_destroy", "hc_batch_run_noalloc", "hc_measure_random_reads",
     "hc_batch_scratch_bytes", "hc_batch_run", "hc_device_view_get", "hc_select",
     "hc_ordered_scratch_bytes", "hc_insert_ordered", "hc_erase_ordered", "hc_apply_mixed",
-    "hc_pack_short3", "hc_unpack_short3",
+    "hc_pack_short3", "hc_unpack_short3", "hc_server_create", "hc_server_run", "hc_server_destroy",
 ]
 
 
@@ -82,6 +82,26 @@ class DeviceView(ctypes.Structure):
                 ("bucket_bytes", ctypes.c_int32), ("hash_mode", ctypes.c_int32), ("pad_from", ctypes.c_int32)]
 
 
+class ServeConfig(ctypes.Structure):
+    """hc_serve_config."""
+    _fields_ = [("lanes", ctypes.c_int32), ("depth", ctypes.c_int32), ("slot_bytes", ctypes.c_int64),
+                ("merge", ctypes.c_int32), ("max_items", ctypes.c_int32), ("batch", BatchConfig)]
+
+
+class Request(ctypes.Structure):
+    """hc_request: one served request."""
+    _fields_ = [("table", ctypes.c_int32), ("op", ctypes.c_int32), ("h_keys", ctypes.c_void_p),
+                ("h_vals", ctypes.c_void_p), ("n", ctypes.c_int64), ("h_status", ctypes.c_void_p),
+                ("h_vals_out", ctypes.c_void_p), ("arrival", ctypes.c_double), ("done", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    """hc_serve_stats."""
+    _fields_ = [("requests", ctypes.c_int64), ("ops", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("queued_max", ctypes.c_int64), ("wall_s", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("p999_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -125,6 +145,9 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_apply_mixed": (i32, [vp, vp, vp, vp, i64, vp, vp, vp]),
         "hc_pack_short3": (i32, [vp, i64, vp, vp]),
         "hc_unpack_short3": (i32, [vp, i64, vp, vp]),
+        "hc_server_create": (i32, [P(vp), P(vp), i32, P(ServeConfig)]),
+        "hc_server_run": (i32, [vp, P(Request), i64, i32, ctypes.c_double, P(ServeStats)]),
+        "hc_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

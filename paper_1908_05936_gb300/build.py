@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          f"-I{os.path.join(ROOT, 'include')}"]
 
-SOURCES = ["hc_api.cu", "hc_batch.cu", "hc_probe.cu", "hc_select.cu", "hc_ordered.cu", "hc_mixed.cu", "hc_kind_set_u32.cu", "hc_kind_set_u64.cu",
+SOURCES = ["hc_api.cu", "hc_batch.cu", "hc_probe.cu", "hc_select.cu", "hc_ordered.cu", "hc_mixed.cu", "hc_serve.cu", "hc_kind_set_u32.cu", "hc_kind_set_u64.cu",
            "hc_kind_map_i64_i32.cu", "hc_kind_map_u64_u64.cu"]
 
 

@@ -100,3 +100,37 @@ def test_examples_library_exports_and_argument_errors(lib):
     assert ex.hcx_apply(ctypes.byref(dv), None, 3, None, None, 1, None, None, None, 128, None) == L.ERR_ARG
     assert ex.hcx_apply(ctypes.byref(dv), None, 0, None, None, 1, None, None, None, 100, None) == L.ERR_ARG
     assert ex.hcx_update_set(ctypes.byref(dv), ctypes.byref(dv), None, 1, None) == L.ERR_ARG
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and
+    field offsets (compiled here with the system C compiler)."""
+    import shutil
+    import subprocess
+    from paper_1908_05936_gb300 import _lib as L
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    checks = {"hc_config": (L.Config, []), "hc_launch": (L.Launch, []), "hc_stats_t": (L.Stats, []),
+              "hc_batch_item": (L.BatchItem, ["d_keys", "n", "d_vals_out"]),
+              "hc_batch_config": (L.BatchConfig, ["use_graph"]),
+              "hc_device_view": (L.DeviceView, ["nb", "kind", "pad_from"]),
+              "hc_predicate": (L.Predicate, ["lo", "box"]),
+              "hc_serve_config": (L.ServeConfig, ["slot_bytes", "batch"]),
+              "hc_request": (L.Request, ["h_keys", "n", "arrival", "done"]),
+              "hc_serve_stats": (L.ServeStats, ["wall_s", "max_ms"])}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hc.h"', "int main(void) {"]
+    for name, (_, fields) in checks.items():
+        lines.append(f'    printf("%zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'    printf("%zu\\n", offsetof({name}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for name, (cls, fields) in checks.items():
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f).offset for f in fields]
+    assert got == want
