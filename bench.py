@@ -78,7 +78,8 @@ def parse():
     ap.add_argument("--workload", default="map_sweep",
                     choices=["map_sweep", "device_api", "multi_table", "served", "rgbd", "set_u32"])
     ap.add_argument("--rgbd-slots", type=int, default=12_500_000)
-    ap.add_argument("--rgbd-hash", type=int, default=1, help="1 = the paper's spatial hash, 0 = mix64")
+    ap.add_argument("--rgbd-hash", type=int, default=1,
+                    help="1 = the paper's spatial hash on packed 21-bit coordinates, 2 = on short3 keys, 0 = mix64")
     ap.add_argument("--tables", type=int, default=1024)
     ap.add_argument("--tile", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=3000)
@@ -674,7 +675,18 @@ def run_rgbd(args):
     gen_s = time.perf_counter() - t0
     capacity = args.rgbd_slots
     tab = Table(L.MAP_I64_I32, capacity, bucket_bytes=args.bucket_bytes or 64, hash_mode=args.rgbd_hash)
-    d_keys = [to_device(k) for k in keys]
+    if args.rgbd_hash == L.HASH_TESCHNER_SHORT3:
+        # the paper's short3 block keys: coordinates repacked into 16-bit fields on the device
+        from paper_1908_05936_gb300.table import pack_short3
+
+        def as_short3(k):
+            u = k.view(np.uint64)
+            c = np.stack([((u >> np.uint64(21 * f)) & np.uint64(0x1FFFFF)).astype(np.int64) for f in range(3)], 1)
+            c = np.where(c >= (1 << 20), c - (1 << 21), c).astype(np.int16)
+            return pack_short3(torch.from_numpy(np.ascontiguousarray(c)).cuda())
+        d_keys = [as_short3(k) for k in keys]
+    else:
+        d_keys = [to_device(k) for k in keys]
     d_vals = [to_device(v) for v in vals]
     found = [torch.empty(len(k), dtype=torch.uint8, device="cuda") for k in keys]
     status = [torch.empty(len(k), dtype=torch.uint8, device="cuda") for k in keys]
