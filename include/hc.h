@@ -194,10 +194,13 @@ HC_API hc_rc hc_erase(hc_table *t, const void *d_keys, int64_t n, uint8_t *d_sta
                void *stream);
 
 /* Host-buffer forms of the three range calls: keys, values and results are
- * HOST arrays.  The library copies them in chunks through device staging
- * buffers that the table allocates on first use and keeps, overlapping the
- * copies with the kernels.  They return after the results are on the host
- * (synchronising `stream`). */
+ * HOST arrays.  When every array of a call is page-locked (cudaHostAlloc or
+ * cudaHostRegister), the kernels read and write them in host memory directly
+ * through their mapped addresses (over NVLink-C2C on a Grace-Blackwell
+ * node): one launch, no copies.  Otherwise the library copies them in chunks
+ * through device staging buffers that the table allocates on first use and
+ * keeps, overlapping the copies with the kernels.  Both return after the
+ * results are on the host (synchronising `stream`). */
 HC_API hc_rc hc_insert_host(hc_table *t, const void *h_keys, const void *h_vals, int64_t n,
                      uint8_t *h_status, void *stream);
 HC_API hc_rc hc_find_host(hc_table *t, const void *h_keys, int64_t n, uint8_t *h_found,

@@ -215,6 +215,18 @@ hc_rc ensure_staging(hc_table *t) {
     return HC_OK;
 }
 
+// The device address of a page-locked host buffer (registered or allocated by
+// CUDA), or nullptr for pageable memory.
+void *mapped(const void *h) {
+    if (!h) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 hc_rc run_host(hc_table *t, int op, const void *h_keys, const void *h_vals, long long n, uint8_t *h_out,
                void *h_vals_out, cudaStream_t s) {
     hc_rc rc = check_table(t);
@@ -224,6 +236,23 @@ hc_rc run_host(hc_table *t, int op, const void *h_keys, const void *h_vals, long
     if (!h_keys) return fail(HC_ERR_ARG, "keys is NULL");
     if (op == hc::OP_INSERT && is_map(t->kind) && !h_vals) return fail(HC_ERR_ARG, "values is NULL");
     if (op == hc::OP_FIND && !h_out) return fail(HC_ERR_ARG, "found flags array is NULL");
+    {
+        // Page-locked buffers: the kernels read the keys and write the results
+        // in host memory directly (over NVLink-C2C on GB300), one launch for
+        // the whole call, no staging copies.
+        const bool want_vals = op == hc::OP_FIND && is_map(t->kind) && h_vals_out;
+        void *dk = mapped(h_keys);
+        void *dv = (op == hc::OP_INSERT && is_map(t->kind)) ? mapped(h_vals) : nullptr;
+        void *dout = mapped(h_out);
+        void *dvo = want_vals ? mapped(h_vals_out) : nullptr;
+        const bool ok = dk && (op != hc::OP_INSERT || !is_map(t->kind) || dv) && (!h_out || dout) &&
+                        (!want_vals || dvo);
+        if (ok) {
+            if ((rc = run_range(t, op, dk, dv, n, static_cast<uint8_t *>(dout), dvo, s)) != HC_OK) return rc;
+            HC_CUDA(cudaStreamSynchronize(s), "synchronising the stream");
+            return HC_OK;
+        }
+    }
     if ((rc = ensure_staging(t)) != HC_OK) return rc;
     const int kb = key_bytes(t->kind), vb = val_bytes(t->kind);
     const long long C = HC_STAGE_CHUNK;

@@ -238,24 +238,38 @@ def test_teschner_hash_and_seeds_do_not_change_results():
         assert np.array_equal(f, outs[0][0]) and np.array_equal(v, outs[0][1])
 
 
+def _pinned(a: np.ndarray) -> np.ndarray:
+    """A page-locked copy of `a` with the same dtype."""
+    out = torch.empty(a.nbytes, dtype=torch.uint8).pin_memory().numpy().view(a.dtype)   # the array keeps the tensor
+    out[:] = a
+    return out
+
+
 @pytest.mark.parametrize("kind", (O.SET_U32, O.MAP_U64_U64))
-def test_host_buffer_calls(kind):
-    """hc_*_host: host arrays in, host results out, chunked staging (two
-    chunks here); same results as the oracle."""
+@pytest.mark.parametrize("pinned", (False, True))
+def test_host_buffer_calls(kind, pinned):
+    """hc_*_host: host arrays in, host results out; pageable arrays go through
+    chunked staging (two chunks here), page-locked ones are read and written
+    in place by the kernels; same results as the oracle."""
     rng = np.random.default_rng(5)
     n = (1 << 22) + 12345
     p = Pair(kind, 1 << 24)
+    host = _pinned if pinned else (lambda a: a)
     try:
         keys = random_keys(kind, n, rng)
         vals = value_for(kind, keys)
-        st = p.g.insert_host(keys, vals)
+        st = host(np.empty(n, np.uint8))
+        p.g.insert_host(host(keys), host(vals) if vals is not None else None, st)
         C.assert_status(keys, st, p.o.insert(keys, vals))
         q = np.concatenate([keys[: n // 2], random_keys(kind, n // 2, rng)])
-        f, v = p.g.find_host(q)
+        f = host(np.empty(len(q), np.uint8))
+        v = host(np.empty(len(q), O.VAL_DTYPE[kind])) if kind in O.VAL_DTYPE else None
+        p.g.find_host(host(q), f, v)
         of, ov = p.o.find(q)
         C.assert_find(f, v, of, ov)
-        st = p.g.erase_host(keys[::2])
-        C.assert_status(keys[::2], st, p.o.erase(keys[::2]))
+        es = host(np.empty(len(keys[::2]), np.uint8))
+        p.g.erase_host(host(np.ascontiguousarray(keys[::2])), es)
+        C.assert_status(keys[::2], es, p.o.erase(keys[::2]))
         p.check()
     finally:
         p.close()
