@@ -371,3 +371,25 @@ def test_streaming_erase(kind, bb, kpt):
         p.check()
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_tombstone_reuse_keeps_keys_unique(kind):
+    """Tiny tables: after an erase, a new key may land in the freed tombstone
+    while a later slot of its bucket stays EMPTY; inserting it again must find
+    it (EXISTS, stored once), a full table overflows, and clear frees it."""
+    rng = np.random.default_rng(2000 + kind)
+    for trial in range(40):
+        p = Pair(kind, 4, bucket_bytes=32)
+        try:
+            keys = random_keys(kind, 8, rng)
+            p.insert(keys[:3], value_for(kind, keys[:3]))
+            p.erase(keys[:1])
+            for k in (keys[3:5], keys[3:5], keys[:1], keys[3:6]):
+                p.insert(k, value_for(kind, k))
+            p.check()
+            p.clear()
+            p.insert(keys, value_for(kind, keys), check=False)
+            assert p.g.size() == min(4, len(set(C.bits(keys).tolist())))
+        finally:
+            p.close()
