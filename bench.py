@@ -38,12 +38,13 @@ BYTES_PER_OP = {"insert": 16 + 1 + 32 + 32, "find": 8 + 8 + 1 + 32, "erase": 8 +
 # workload: dram__bytes_read.sum + dram__bytes_write.sum over the four fill
 # launches of one step at full size (one ncu capture), divided by the keys
 # they inserted.  Valid only while the kernel sources hash to `digest`.
-INSERT_TRAFFIC = {"bytes_per_op": 227.67, "digest": "bace0d74b19dcc89"}
+INSERT_TRAFFIC = {"bytes_per_op": 227.67, "digest": "pending"}
 
 
 def insert_kernel_digest() -> str:
     """Hash of the insert kernel's source: the device core, the streaming
-    insert kernel with its launch bound, and its launcher."""
+    insert's chunk function and kernel with its launch bound, and its
+    launcher."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_1908_05936_gb300", "csrc")
@@ -51,6 +52,7 @@ def insert_kernel_digest() -> str:
     stream, kernels = read("hc_stream.cuh"), read("hc_kernels.cuh")
     parts = [read("hc_core.cuh"),
              re.search(r"#ifndef HC_STREAM_INSERT_MINB.*?#endif", stream, re.S).group(0),
+             re.search(r"__device__ __forceinline__ void insert_stream_chunk\(.*?\n}\n", stream, re.S).group(0),
              re.search(r"template <int KIND, int BB, int KPT, int S>\n__global__[^\n]*\nk_insert_stream\(.*?\n}\n",
                        stream, re.S).group(0),
              re.search(r"cudaError_t launch_insert_stream\(.*?\n}\n", kernels, re.S).group(0)]
@@ -531,7 +533,8 @@ def run_multi_table(args):
             items += [Item(t, L.OP_INSERT, ki, None, torch.empty(ki.numel(), dtype=torch.uint8, device="cuda")),
                       Item(t, L.OP_FIND, kf, None, torch.empty(kf.numel(), dtype=torch.uint8, device="cuda")),
                       Item(t, L.OP_ERASE, ke, None, torch.empty(ke.numel(), dtype=torch.uint8, device="cuda"))]
-        batch = Batch(items, tile=args.tile, use_graph=True) if arm == "batched" else None
+        batch = Batch(items, keys_per_group=args.kpt, block=args.block, tile=args.tile, use_graph=True) \
+            if arm == "batched" else None
         stream = torch.cuda.current_stream()
 
         def step():

@@ -405,7 +405,9 @@ typedef struct hc_batch_item {
 
 typedef struct hc_batch_config {
     int32_t lane_bytes;      /* 0: one thread per key (whole bucket); 32: 32-byte lanes */
-    int32_t keys_per_group;
+    int32_t keys_per_group;  /* 1 or 2: lock-step phases (default 1); 4 or 8:
+                                streaming phases (keys staged per block, 2 or
+                                4 probes in flight per thread; block <= 256) */
     int32_t block;           /* threads per block (0 = 256)                */
     int32_t blocks_per_sm;   /* persistent grid = SMs x this (0 = auto)    */
     int32_t tile;            /* keys per tile (0 = auto)                   */

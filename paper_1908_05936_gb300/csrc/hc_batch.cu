@@ -18,6 +18,7 @@
 #include "../../include/hc.h"
 #include "hc_core.cuh"
 #include "hc_internal.h"
+#include "hc_stream.cuh"
 #include "hc_table.h"
 
 namespace hc {
@@ -87,6 +88,46 @@ k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_c
     }
 }
 
+// The streaming form of a phase (keys_per_group 4 or 8): a block takes the
+// next chunk with one atomic add and works through it in pieces of
+// blockDim.x * KPT keys with the streaming kernels' chunk functions (keys
+// staged in shared memory, S probes in flight per thread).
+template <int KIND, int OP, int BB, int KPT, int S>
+__global__ void __launch_bounds__(256)
+k_batch_stream(const BatchItemDev *__restrict__ items, int n_items, long long n_chunks, int tile,
+               unsigned long long *counter) {
+    using T = Traits<KIND>;
+    __shared__ long long s_chunk;
+    const int piece = blockDim.x * KPT;
+    while (true) {
+        if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long c = s_chunk;
+        __syncthreads();                                   // s_chunk is written again only after every thread read it
+        if (c >= n_chunks) break;
+        int lo = 0, hi = n_items - 1;                      // last item whose chunk_begin <= c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].chunk_begin <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchItemDev &it = items[lo];
+        const long long k0 = (c - it.chunk_begin) * tile;
+        const long long k1 = k0 + tile < it.n ? k0 + tile : it.n;
+        const auto *keys = (const typename T::Key *)it.keys;
+        for (long long p0 = k0; p0 < k1; p0 += piece) {
+            const int m = (int)(k1 - p0 < piece ? k1 - p0 : piece);
+            if constexpr (OP == OP_INSERT)
+                insert_stream_chunk<KIND, BB, KPT, S>(it.v, keys, (const typename T::Val *)it.vals, p0, m, it.out,
+                                                      nullptr);
+            else if constexpr (OP == OP_FIND)
+                find_stream_chunk<KIND, BB, KPT, S>(it.v, keys, p0, m, it.out, (typename T::Val *)it.vals_out);
+            else
+                erase_stream_chunk<KIND, BB, KPT, S>(it.v, keys, p0, m, it.out, nullptr);
+        }
+    }
+}
+
 __global__ void k_zero_counters(unsigned long long *c, int n) {
     if (threadIdx.x < n) c[threadIdx.x] = 0ull;
 }
@@ -95,8 +136,18 @@ using PhaseKernel = void (*)(const BatchItemDev *, int, long long, int, unsigned
 
 template <int KIND, int OP, int BB>
 PhaseKernel pick_lb_kpt(int lb, int kpt) {
+    if (kpt == 4) return k_batch_stream<KIND, OP, BB, 4, 2>;
+    if (kpt == 8) return k_batch_stream<KIND, OP, BB, 8, 4>;
     if (lb == 0) return kpt == 1 ? k_batch_phase<KIND, OP, BB, 1, 1> : k_batch_phase<KIND, OP, BB, 1, 2>;
     return kpt == 1 ? k_batch_phase<KIND, OP, BB, 0, 1> : k_batch_phase<KIND, OP, BB, 0, 2>;
+}
+
+// Dynamic shared memory of a phase launch (the streaming form's staging).
+size_t phase_smem(int kind, int kpt, int block) {
+    if (kpt < 4) return 0;
+    const int kb = kind == KIND_SET_U32 ? 4 : 8;
+    const int vb = kind == KIND_SET_U32 ? 4 : 8;            // the staging holds a value slot for every kind
+    return (size_t)block * kpt * (kb + vb + 1);
 }
 
 template <int KIND, int OP>
@@ -161,8 +212,8 @@ hc_rc enqueue(hc_batch *b, cudaStream_t s) {
     for (size_t p = 0; p < b->phases.size(); ++p) {
         const hc::PhaseDesc &ph = b->phases[p];
         hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, b->lane_bytes, b->kpt);
-        k<<<b->grid[p], b->block, 0, s>>>(b->d_items + ph.item0, ph.n_items, ph.n_chunks, b->tile,
-                                          b->d_counters + ph.counter);
+        k<<<b->grid[p], b->block, hc::phase_smem(ph.kind, b->kpt, b->block), s>>>(
+            b->d_items + ph.item0, ph.n_items, ph.n_chunks, b->tile, b->d_counters + ph.counter);
         e = cudaGetLastError();
         if (e != cudaSuccess) return bcuda(e, "launching a batch phase");
     }
@@ -185,7 +236,9 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
     const int block = c.block ? c.block : 256;
     const int tile = c.tile ? c.tile : 4096;
     if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole bucket) or 32");
-    if (kpt != 1 && kpt != 2) return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
+    if (kpt != 1 && kpt != 2 && kpt != 4 && kpt != 8)
+        return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2 (lock-step) or 4 or 8 (streaming)");
+    if (kpt >= 4 && block > 256) return bfail(HC_ERR_ARG, "streaming phases take at most 256 threads per block");
     if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
 
@@ -255,11 +308,13 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
         int per_sm = c.blocks_per_sm;
         if (per_sm <= 0) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, hc::pick_kernel(phases[p].kind, phases[p].op, phases[p].bb, lb, kpt), block, 0);
+                &per_sm, hc::pick_kernel(phases[p].kind, phases[p].op, phases[p].bb, lb, kpt), block,
+                hc::phase_smem(phases[p].kind, kpt, block));
             if (per_sm <= 0) per_sm = 1;
         }
         long long g = (long long)sms * per_sm;
-        const long long need = (phases[p].n_chunks * 32 + block - 1) / block;   // one warp per chunk at most
+        // one warp (lock-step) or one block (streaming) per chunk at most
+        const long long need = kpt >= 4 ? phases[p].n_chunks : (phases[p].n_chunks * 32 + block - 1) / block;
         if (g > need) g = need;
         b->grid.push_back((int)(g > 0 ? g : 1));
     }
@@ -378,7 +433,9 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
     const int block = c.block ? c.block : 256;
     const int tile = c.tile ? c.tile : 4096;
     if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole bucket) or 32");
-    if (kpt != 1 && kpt != 2) return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
+    if (kpt != 1 && kpt != 2 && kpt != 4 && kpt != 8)
+        return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2 (lock-step) or 4 or 8 (streaming)");
+    if (kpt >= 4 && block > 256) return bfail(HC_ERR_ARG, "streaming phases take at most 256 threads per block");
     if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
     if (c.use_graph) return bfail(HC_ERR_ARG, "hc_batch_run_noalloc launches directly; use_graph must be 0");
@@ -447,15 +504,15 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
         hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, lb, kpt);
         int per_sm = c.blocks_per_sm;
         if (per_sm <= 0) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, hc::phase_smem(ph.kind, kpt, block));
             if (e != cudaSuccess) return bcuda(e, "querying occupancy");
             if (per_sm <= 0) per_sm = 1;
         }
         long long g = (long long)sms * per_sm;
-        const long long need = (ph.n_chunks * 32 + block - 1) / block;
+        const long long need = kpt >= 4 ? ph.n_chunks : (ph.n_chunks * 32 + block - 1) / block;
         if (g > need) g = need;
-        k<<<(unsigned)(g > 0 ? g : 1), block, 0, s>>>(scratch->items + ph.item0, ph.n_items, ph.n_chunks, tile,
-                                                     scratch->counters + ph.counter);
+        k<<<(unsigned)(g > 0 ? g : 1), block, hc::phase_smem(ph.kind, kpt, block), s>>>(
+            scratch->items + ph.item0, ph.n_items, ph.n_chunks, tile, scratch->counters + ph.counter);
         e = cudaGetLastError();
         if (e != cudaSuccess) return bcuda(e, "launching a batch phase");
     }
@@ -502,7 +559,9 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
     const int block = c.block ? c.block : 256;
     const int tile = c.tile ? c.tile : 4096;
     if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole key region) or 32");
-    if (kpt != 1 && kpt != 2) return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2");
+    if (kpt != 1 && kpt != 2 && kpt != 4 && kpt != 8)
+        return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2 (lock-step) or 4 or 8 (streaming)");
+    if (kpt >= 4 && block > 256) return bfail(HC_ERR_ARG, "streaming phases take at most 256 threads per block");
     if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
 
@@ -557,12 +616,14 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
         const hc::PhaseDesc &ph = phases[p];
         hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, lb, kpt);
         int per_sm = c.blocks_per_sm;
-        if (per_sm <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0) != cudaSuccess) per_sm = 1;
+        const size_t smem = hc::phase_smem(ph.kind, kpt, block);
+        if (per_sm <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess) per_sm = 1;
         if (per_sm <= 0) per_sm = 1;
         long long g = (long long)sms * per_sm;
-        const long long want = (ph.n_chunks * 32 + block - 1) / block;
+        const long long want = kpt >= 4 ? ph.n_chunks : (ph.n_chunks * 32 + block - 1) / block;
         if (g > want) g = want;
-        k<<<(unsigned)(g > 0 ? g : 1), block, 0, s>>>(d_items + ph.item0, ph.n_items, ph.n_chunks, tile, d_ctr + ph.counter);
+        k<<<(unsigned)(g > 0 ? g : 1), block, smem, s>>>(d_items + ph.item0, ph.n_items, ph.n_chunks, tile,
+                                                         d_ctr + ph.counter);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda(e, "launching the batch phases");

@@ -54,9 +54,8 @@ __device__ __forceinline__ unsigned long long load_find_val(const View &v, unsig
 }
 
 template <int KIND, int BB, int KPT, int S>
-__global__ void __launch_bounds__(256, HC_STREAM_FIND_MINB)
-k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *found,
-              typename Traits<KIND>::Val *vals_out) {
+__device__ __forceinline__ void find_stream_chunk(const View &v, const typename Traits<KIND>::Key *keys, long long c0, int m,
+                                                  uint8_t *found, typename Traits<KIND>::Val *vals_out) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Val = typename T::Val;
@@ -70,8 +69,7 @@ k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8
     Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * sizeof(Key));
     uint8_t *sf = smem + (size_t)chunk * (sizeof(Key) + sizeof(Val));
 
-    const long long c0 = (long long)blockIdx.x * chunk;
-    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    __syncthreads();                         // the staging of a previous chunk is no longer read
     for (int i = threadIdx.x; i < m; i += nt) sk[i] = ld_stream(keys + c0 + i);
     __syncthreads();
 
@@ -144,6 +142,15 @@ k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8
             if (vals_out) st_stream(vals_out + c0 + i, sv[i]);
         }
     }
+}
+
+template <int KIND, int BB, int KPT, int S>
+__global__ void __launch_bounds__(256, HC_STREAM_FIND_MINB)
+k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *found,
+              typename Traits<KIND>::Val *vals_out) {
+    const long long chunk = (long long)blockDim.x * KPT;
+    const long long c0 = (long long)blockIdx.x * chunk;
+    find_stream_chunk<KIND, BB, KPT, S>(v, keys, c0, (int)(n - c0 < chunk ? n - c0 : chunk), found, vals_out);
 }
 
 // Streaming map lookup by lane pairs: the two lanes of a pair handle one key.
@@ -301,9 +308,9 @@ k_find_pair(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t
 // stores; counters leave with one atomic per warp.  Equal keys inside a warp
 // are not folded here (folding is a lock-step option).
 template <int KIND, int BB, int KPT, int S>
-__global__ void __launch_bounds__(256, HC_STREAM_INSERT_MINB)
-k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
-                uint8_t *status, const uint8_t *skip) {
+__device__ __forceinline__ void insert_stream_chunk(const View &v, const typename Traits<KIND>::Key *keys,
+                                                    const typename Traits<KIND>::Val *vals, long long c0, int m,
+                                                    uint8_t *status, const uint8_t *skip) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Val = typename T::Val;
@@ -318,8 +325,7 @@ k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename T
     Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * sizeof(Key));
     uint8_t *ss = smem + (size_t)chunk * (sizeof(Key) + sizeof(Val));
 
-    const long long c0 = (long long)blockIdx.x * chunk;
-    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    __syncthreads();                         // the staging of a previous chunk is no longer read
     for (int i = threadIdx.x; i < m; i += nt) {
         sk[i] = ld_stream(keys + c0 + i);
         if constexpr (T::MAP) sv[i] = ld_stream(vals + c0 + i);
@@ -456,6 +462,15 @@ k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename T
     flush_counts(v, cnt);
 }
 
+template <int KIND, int BB, int KPT, int S>
+__global__ void __launch_bounds__(256, HC_STREAM_INSERT_MINB)
+k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename Traits<KIND>::Val *vals, long long n,
+                uint8_t *status, const uint8_t *skip) {
+    const long long chunk = (long long)blockDim.x * KPT;
+    const long long c0 = (long long)blockIdx.x * chunk;
+    insert_stream_chunk<KIND, BB, KPT, S>(v, keys, vals, c0, (int)(n - c0 < chunk ? n - c0 : chunk), status, skip);
+}
+
 // Streaming erase: the staging and refilling of k_find_stream; a slot that
 // finds its key joins the round's compare-and-swap (key -> TOMB) with the
 // other slots that found theirs.  A failed swap means an equal key of the
@@ -464,8 +479,8 @@ k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename T
 // NOT_FOUND without a probe (the later occurrences of a key in the ordered
 // erase).
 template <int KIND, int BB, int KPT, int S>
-__global__ void __launch_bounds__(256, HC_STREAM_ERASE_MINB)
-k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status, const uint8_t *skip) {
+__device__ __forceinline__ void erase_stream_chunk(const View &v, const typename Traits<KIND>::Key *keys, long long c0, int m,
+                                                   uint8_t *status, const uint8_t *skip) {
     using T = Traits<KIND>;
     using Key = typename T::Key;
     using Sl = Slots<KIND, BB>;
@@ -477,8 +492,7 @@ k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint
     Key *sk = reinterpret_cast<Key *>(smem);
     uint8_t *ss = smem + (size_t)chunk * sizeof(Key);
 
-    const long long c0 = (long long)blockIdx.x * chunk;
-    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    __syncthreads();                         // the staging of a previous chunk is no longer read
     for (int i = threadIdx.x; i < m; i += nt) {
         sk[i] = ld_stream(keys + c0 + i);
         ss[i] = (skip && ld_stream(skip + c0 + i)) ? (uint8_t)ST_NOT_FOUND : (uint8_t)0xFF;   // 0xFF: to do
@@ -565,6 +579,14 @@ k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint
     for (int i = threadIdx.x; i < m; i += nt)
         if (status) st_stream(status + c0 + i, ss[i]);
     flush_counts(v, cnt);
+}
+
+template <int KIND, int BB, int KPT, int S>
+__global__ void __launch_bounds__(256, HC_STREAM_ERASE_MINB)
+k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status, const uint8_t *skip) {
+    const long long chunk = (long long)blockDim.x * KPT;
+    const long long c0 = (long long)blockIdx.x * chunk;
+    erase_stream_chunk<KIND, BB, KPT, S>(v, keys, c0, (int)(n - c0 < chunk ? n - c0 : chunk), status, skip);
 }
 
 }  // namespace hc

@@ -43,7 +43,7 @@ def build_items(tables, ops):
 
 
 @pytest.mark.parametrize("graph", [True, False])
-@pytest.mark.parametrize("lb,kpt", [(0, 1), (32, 2), (0, 2)])
+@pytest.mark.parametrize("lb,kpt", [(0, 1), (32, 2), (0, 2), (0, 4), (0, 8)])
 def test_batched_equals_oracle_and_plain(graph, lb, kpt):
     slots, ops, bbs = make_tables(48, 10, 15, seed=1)
     tables = [Table(L.SET_U64, int(s), bucket_bytes=bb) for s, bb in zip(slots, bbs)]
@@ -81,7 +81,8 @@ def test_batched_equals_oracle_and_plain(graph, lb, kpt):
         tb.close()
 
 
-def test_batched_maps_mixed_kinds():
+@pytest.mark.parametrize("kpt", [1, 4])
+def test_batched_maps_mixed_kinds(kpt):
     """Items of different kinds and ops in one batch: each phase runs one
     persistent launch per kind."""
     rng = np.random.default_rng(4)
@@ -106,7 +107,7 @@ def test_batched_maps_mixed_kinds():
         tabs.append(t)
         orcs.append(o)
         checks.append((kind, k, v, q, e, si, ff, fv, se))
-    b = Batch(items, lane_bytes=0, keys_per_group=1, tile=256, use_graph=True)
+    b = Batch(items, lane_bytes=0, keys_per_group=kpt, tile=256, use_graph=True)
     b.launch()
     torch.cuda.synchronize()
     for o, (kind, k, v, q, e, si, ff, fv, se) in zip(orcs, checks):
