@@ -38,7 +38,7 @@ BYTES_PER_OP = {"insert": 16 + 1 + 32 + 32, "find": 8 + 8 + 1 + 32, "erase": 8 +
 # workload: dram__bytes_read.sum + dram__bytes_write.sum over the four fill
 # launches of one step at full size (one ncu capture), divided by the keys
 # they inserted.  Valid only while the kernel sources hash to `digest`.
-INSERT_TRAFFIC = {"bytes_per_op": 227.67, "digest": "pending"}
+INSERT_TRAFFIC = {"bytes_per_op": 227.68, "digest": "2dc36df6c4a95205"}
 
 
 def insert_kernel_digest() -> str:
