@@ -490,17 +490,32 @@ def run_oracle_sample(args, sample_log2: int):
     miss = recipes.map_miss_keys(q, start=n)
     er = recipes.map_hit_keys(n, q, salt=1)
     t = O.OracleTable(O.MAP_U64_U64, 1 << args.slots_log2)
+    per = {}
     t0 = time.perf_counter()
-    t.insert(fill, vals)
-    t.find(hit)
-    t.find(miss)
-    t.erase(er)
+    for name, fn, cnt in (("insert", lambda: t.insert(fill, vals), n), ("find_hit", lambda: t.find(hit), q),
+                          ("find_miss", lambda: t.find(miss), q), ("erase", lambda: t.erase(er), q)):
+        a = time.perf_counter()
+        fn()
+        per[name] = round(cnt / (time.perf_counter() - a) / 1e6, 3)
     dt = time.perf_counter() - t0
     t.close()
     ops = n + 3 * q
     return {"value": round(ops / dt / 1e6, 3), "unit": "Mops/s", "cores": 1, "kind": "oracle",
             "sample": f"fill {n} keys, find {q} hit + {q} miss, erase {q} (single-threaded C chained table)",
-            "seconds": round(dt, 2), "host_cores_available": os.cpu_count()}
+            "seconds": round(dt, 2), "ops_mops": per, "host_cores_available": os.cpu_count(),
+            "host_cpu": host_cpu()}
+
+
+def host_cpu() -> str:
+    """The host CPU's model name (lscpu), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
 
 
 # ------------------------------------------------ multi-table workload --
