@@ -70,3 +70,19 @@ def test_served_equals_alone(merge):
         C.assert_contents(ka, va, kb, vb)
     for t in mix_tabs + alone_tabs:
         t.close()
+
+
+def test_server_timeout_reports_and_recovers():
+    """A run that cannot finish within its time limit returns HC_ERR_STATE
+    after waiting for its launches; the same server then serves normally."""
+    n_tables, slots = 2, 1 << 16
+    tabs = make_tables(n_tables, slots, 1 << 12, seed=5)
+    srv = Server(tabs, slot_bytes=1 << 20, lanes=2, merge=True, depth=2, max_items=4)
+    reqs = make_requests(20, n_tables, rate=1e6, seed=6, max_log2=10)
+    with pytest.raises(L.HCError):
+        srv.run(reqs, realtime=True, timeout_s=0.0)
+    stats = srv.run(make_requests(20, n_tables, rate=1e6, seed=7, max_log2=10), realtime=False)
+    assert stats["requests"] == 20
+    srv.close()
+    for t in tabs:
+        t.close()
