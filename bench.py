@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=24)
     ap.add_argument("--workload", default="map_sweep",
-                    choices=["map_sweep", "device_api", "multi_table", "served", "rgbd", "set_u32"])
+                    choices=["map_sweep", "map_grid", "device_api", "multi_table", "served", "rgbd", "set_u32"])
     ap.add_argument("--rgbd-slots", type=int, default=12_500_000)
     ap.add_argument("--rgbd-hash", type=int, default=1,
                     help="1 = the paper's spatial hash on packed 21-bit coordinates, 2 = on short3 keys, 0 = mix64")
@@ -658,6 +658,78 @@ def run_set_u32(args):
             "clear_ms": round(med["clear"], 4), "final_size": size, "gpu_launches": 4 * args.steps}
 
 
+# ---------------------------------------- load-factor x batch-size grid --
+
+def run_map_grid(args):
+    """map<u64,u64>, 2^28 slots: for every batch size 2^16 .. 2^26 and load
+    factor 0.5 / 0.7 / 0.8 / 0.9, clear, fill to the load factor in batches of
+    that size, then find 2^26 present and 2^26 absent keys and erase 2^26
+    present keys (one call each).  CUDA events around every call; the 4 GiB
+    table is far larger than L2.  Prints one line with the whole grid."""
+    import torch
+    from paper_1908_05936_gb300 import _lib as L
+    from paper_1908_05936_gb300 import build
+    from paper_1908_05936_gb300.table import Table
+    from workloads import gpu as G
+    from workloads import recipes
+
+    build.build()
+    slots = 1 << args.slots_log2
+    q = 1 << 26
+    n_max = recipes.fill_count(slots, 0.9)
+    fill = G.stream_u64(3, 0, 0, n_max)
+    vals = G.value_of(fill)
+    miss = G.stream_u64(4, 0, 0, q)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    st = torch.empty(q, dtype=torch.uint8, device="cuda")
+    vo = torch.empty(q, dtype=torch.int64, device="cuda")
+    t = Table(L.MAP_U64_U64, slots, bucket_bytes=args.bucket_bytes or 64)
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        return a, b
+
+    grid = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for blog in (16, 18, 20, 22, 24, 26):
+        B = 1 << blog
+        for lf in (0.5, 0.7, 0.8, 0.9):
+            n = recipes.fill_count(slots, lf)
+            t.clear()
+            torch.cuda.synchronize()
+            ins = []
+            for off in range(0, n, B):
+                m = min(B, n - off)
+                ins.append((m, *timed(lambda: t.insert(fill[off:off + m], vals[off:off + m], status=st[:m]))))
+            hit = fill[torch.randperm(n, device="cuda", generator=gen)[:q]]
+            fh = timed(lambda: t.find(hit, found=st, vals_out=vo))
+            fm = timed(lambda: t.find(miss, found=st, vals_out=vo))
+            er = timed(lambda: t.erase(hit, status=st))
+            torch.cuda.synchronize()
+            ins_ms = sum(a.elapsed_time(b) for _, a, b in ins)
+            grid.append({"batch": B, "load_factor": lf, "insert_gops": round(n / ins_ms / 1e6, 2),
+                         "insert_launches": len(ins), "find_hit_gops": round(q / fh[0].elapsed_time(fh[1]) / 1e6, 2),
+                         "find_miss_gops": round(q / fm[0].elapsed_time(fm[1]) / 1e6, 2),
+                         "erase_gops": round(q / er[0].elapsed_time(er[1]) / 1e6, 2),
+                         "size_ok": t.size() == n - q})
+    clk = clocks.stop()
+    t.close()
+    head = [g for g in grid if g["batch"] == 1 << 26 and g["load_factor"] == 0.8][0]
+    return {"metric": "insert / find / erase G ops/s over load factor and batch size", "value": head["insert_gops"],
+            "unit": "G ops/s (insert, LF 0.8, batch 2^26)", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded splitmix64 keys)",
+            "config": {"workload": f"map<u64,u64> {slots} slots, LF 0.5/0.7/0.8/0.9 x batches 2^16..2^26, "
+                                   "find 2^26 present + 2^26 absent, erase 2^26",
+                       "l2": "inputs larger than L2 (4 GiB table)"},
+            "grid": grid, "clocks": clk}
+
+
 # ------------------------------------------------------ RGB-D workload --
 
 def rgbd_frames(params, workers: int = 8):
@@ -845,6 +917,9 @@ def main():
         return
     if args.workload == "set_u32":
         print(json.dumps(run_set_u32(args)))
+        return
+    if args.workload == "map_grid":
+        print(json.dumps(run_map_grid(args)))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
