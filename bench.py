@@ -684,6 +684,8 @@ def run_map_grid(args):
     st = torch.empty(q, dtype=torch.uint8, device="cuda")
     vo = torch.empty(q, dtype=torch.int64, device="cuda")
     t = Table(L.MAP_U64_U64, slots, bucket_bytes=args.bucket_bytes or 64)
+    for op in (0, 1, 2):
+        t.set_launch(op, lane_bytes=args.lane_bytes, keys_per_group=args.kpt, block=args.block)
     s = torch.cuda.current_stream()
 
     def timed(fn):

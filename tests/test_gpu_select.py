@@ -108,3 +108,24 @@ def test_select_appends_and_counts_past_cap(kind):
         assert len(np.unique(sk)) == 1000 and np.isin(sk, ok).all()
     finally:
         p.close()
+
+
+def test_select_edges():
+    """Empty table, zero capacity (count only), a predicate matching nothing,
+    and a table holding only the two side-slot keys."""
+    p = Pair(O.MAP_U64_U64, 1000, bucket_bytes=64)
+    try:
+        ko, vo, cnt = p.g.select(L.PRED_ALL, cap=0, keys_out=torch.empty(0, dtype=torch.int64, device="cuda"))
+        assert int(cnt.item()) == 0
+        keys = np.array(RESERVED[O.MAP_U64_U64])
+        p.insert(keys, value_for(O.MAP_U64_U64, keys))
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        p.g.select(L.PRED_ALL, keys_out=torch.empty(0, dtype=torch.int64, device="cuda"), count=cnt, cap=0)
+        assert int(cnt.item()) == 2                      # counted, nothing written
+        gk, gv, n = _gpu_select(p, kind=L.PRED_ALL)
+        ok, ov = p.o.select(O.PRED_ALL)
+        _assert_same(p, gk, gv, ok, ov)
+        gk, gv, n = _gpu_select(p, kind=L.PRED_KEY_RANGE, lo=0, hi=2**62)
+        assert n == 0
+    finally:
+        p.close()

@@ -12,7 +12,7 @@ from gpu_pair import Pair, value_for
 from oracle import oracle as O
 from paper_1908_05936_gb300 import _lib as L
 from paper_1908_05936_gb300 import device_api as D
-from paper_1908_05936_gb300.table import pack_short3, to_device, to_numpy, unpack_short3
+from paper_1908_05936_gb300.table import Table, pack_short3, to_device, to_numpy, unpack_short3
 
 pytestmark = pytest.mark.gpu
 
@@ -85,3 +85,16 @@ def test_in_kernel_functions_on_short3_map():
         p.check()
     finally:
         p.close()
+
+
+def test_mixed_and_pack_empty_calls():
+    """n = 0 is a no-op for the mixed batch and the short3 conversions."""
+    t = Table(O.SET_U64, 100)
+    try:
+        e = torch.empty(0, dtype=torch.int64, device="cuda")
+        st, _ = t.apply_mixed(torch.empty(0, dtype=torch.uint8, device="cuda"), e)
+        assert st.numel() == 0
+        assert unpack_short3(e).shape == (0, 3)
+        assert t.size() == 0
+    finally:
+        t.close()
