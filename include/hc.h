@@ -116,8 +116,9 @@ typedef struct hc_config {
  * each thread keeps 2 or 4 probes in flight, refilling as they finish (no
  * duplicate folding in this form).  Defaults:
  * lane_bytes = the bucket's key region (one thread per key),
- * keys_per_group 4 (streaming), block 64, folding off.  Results never depend on the
- * shape. */
+ * keys_per_group 4 (streaming), block 64, folding off; until hc_set_launch
+ * sets an op's shape, inserts of fewer than 8192 keys per multiprocessor run
+ * one key per thread in lock step.  Results never depend on the shape. */
 typedef struct hc_launch {
     int32_t lane_bytes;       /* 32, 64 or 128, at most bucket_bytes     */
     int32_t keys_per_group;   /* 1 or 2; 4 or 8: streaming forms       */

@@ -21,6 +21,7 @@ struct hc_table {
     void *d_mem;          // header followed by the slots
     hc::View view;
     hc::LaunchShape shape[3];
+    bool shape_set[3] = {false, false, false};   // hc_set_launch was called for the op
     uint32_t *locks = nullptr;   // lock bits of the in-kernel map insert (one per bucket), on first use
     // staging for the host-buffer calls (allocated on first use)
     void *stage_mem = nullptr;
