@@ -532,53 +532,6 @@ namespace {
 constexpr int kRunMaxItems = 4096;
 thread_local hc::BatchItemDev t_run_items[kRunMaxItems];
 
-// Page-locked copies of the descriptors, so that their copy to the device is
-// asynchronous (a copy from pageable memory waits for the stream first,
-// which would stall a caller that keeps several launches in flight).  A ring
-// per host thread; an entry is rewritten only after the copy that read it
-// has completed (its event).
-constexpr int kRing = 8;
-struct DescRing {
-    hc::BatchItemDev *buf[kRing] = {};
-    cudaEvent_t done[kRing] = {};
-    bool used[kRing] = {};
-    int next = 0;
-    bool ok = false;
-    ~DescRing() {
-        for (int i = 0; i < kRing; ++i) {
-            if (done[i]) cudaEventDestroy(done[i]);
-            if (buf[i]) cudaFreeHost(buf[i]);
-        }
-    }
-};
-thread_local DescRing t_ring;
-
-// A page-locked buffer for n descriptors, or nullptr (then the pageable
-// copy is used).
-hc::BatchItemDev *ring_take(int n, int *slot) {
-    if (!t_ring.ok) {
-        t_ring.ok = true;
-        for (int i = 0; i < kRing; ++i) {
-            if (cudaHostAlloc(reinterpret_cast<void **>(&t_ring.buf[i]), sizeof(hc::BatchItemDev) * kRunMaxItems,
-                              cudaHostAllocPortable) != cudaSuccess ||
-                cudaEventCreateWithFlags(&t_ring.done[i], cudaEventDisableTiming) != cudaSuccess) {
-                (void)cudaGetLastError();
-                t_ring.ok = false;
-                return nullptr;
-            }
-        }
-    }
-    if (n > kRunMaxItems) return nullptr;
-    const int r = t_ring.next;
-    t_ring.next = (r + 1) % kRing;
-    if (t_ring.used[r] && cudaEventSynchronize(t_ring.done[r]) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return nullptr;
-    }
-    *slot = r;
-    return t_ring.buf[r];
-}
-
 }  // namespace
 
 extern "C" {
@@ -656,16 +609,7 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
     auto *d_items = static_cast<hc::BatchItemDev *>(d_scratch);
     auto *d_ctr = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_scratch) + need - 512);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int ring_slot = -1;
-    hc::BatchItemDev *pinned = ring_take(n_dev, &ring_slot);
-    if (pinned) {
-        std::memcpy(pinned, t_run_items, (size_t)n_dev * sizeof(hc::BatchItemDev));
-        e = cudaMemcpyAsync(d_items, pinned, (size_t)n_dev * sizeof(hc::BatchItemDev), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaEventRecord(t_ring.done[ring_slot], s);
-        if (e == cudaSuccess) t_ring.used[ring_slot] = true;
-    } else {
-        e = cudaMemcpyAsync(d_items, t_run_items, (size_t)n_dev * sizeof(hc::BatchItemDev), cudaMemcpyHostToDevice, s);
-    }
+    e = cudaMemcpyAsync(d_items, t_run_items, (size_t)n_dev * sizeof(hc::BatchItemDev), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return bcuda(e, "copying the batch descriptors");
     hc::k_zero_counters<<<1, 64, 0, s>>>(d_ctr, n_phases);
     for (int p = 0; p < n_phases; ++p) {
