@@ -541,8 +541,19 @@ HC_API int64_t hc_batch_scratch_bytes(int64_t n_items) {
     return (int64_t)((n_items * sizeof(hc::BatchItemDev) + 255) / 256 * 256 + 512);   // + 36 counters
 }
 
+namespace {
+hc_rc batch_run(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg, void *d_scratch,
+                int64_t scratch_bytes, void *h_pinned, void *stream);
+}
+
 HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg, void *d_scratch,
                           int64_t scratch_bytes, void *stream) {
+    return batch_run(items, n_items, cfg, d_scratch, scratch_bytes, nullptr, stream);
+}
+
+namespace {
+hc_rc batch_run(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg, void *d_scratch,
+                int64_t scratch_bytes, void *h_pinned, void *stream) {
     if (n_items < 0 || (n_items > 0 && !items)) return bfail(HC_ERR_ARG, "bad item list");
     if (n_items > kRunMaxItems)
         return bfail(HC_ERR_ARG, "hc_batch_run takes at most 4096 items per call (got " +
@@ -565,6 +576,7 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
     if (block < 64 || block > 256 || block % 32) return bfail(HC_ERR_ARG, "block must be a multiple of 32 in [64, 256]");
     if (tile < 128 || tile % 128) return bfail(HC_ERR_ARG, "tile must be a positive multiple of 128");
 
+    hc::BatchItemDev *desc = h_pinned ? static_cast<hc::BatchItemDev *>(h_pinned) : t_run_items;
     hc::PhaseDesc phases[36];
     int n_phases = 0, n_dev = 0;
     for (int op = 0; op < 3; ++op) {
@@ -583,7 +595,7 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
                     return bfail(HC_ERR_ARG, "item keys NULL or misaligned");
                 if (op == HC_OP_INSERT && map && !it.d_vals) return bfail(HC_ERR_ARG, "insert item on a map without values");
                 if (op == HC_OP_FIND && !it.d_out) return bfail(HC_ERR_ARG, "find item without a found array");
-                hc::BatchItemDev &d = t_run_items[n_dev++];
+                hc::BatchItemDev &d = desc[n_dev++];
                 d = hc::BatchItemDev{};
                 d.v = it.table->view;
                 d.v.rotate = it.n > (long long)d.v.nb ? 1 : 0;
@@ -609,7 +621,7 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
     auto *d_items = static_cast<hc::BatchItemDev *>(d_scratch);
     auto *d_ctr = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_scratch) + need - 512);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    e = cudaMemcpyAsync(d_items, t_run_items, (size_t)n_dev * sizeof(hc::BatchItemDev), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(d_items, desc, (size_t)n_dev * sizeof(hc::BatchItemDev), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return bcuda(e, "copying the batch descriptors");
     hc::k_zero_counters<<<1, 64, 0, s>>>(d_ctr, n_phases);
     for (int p = 0; p < n_phases; ++p) {
@@ -629,5 +641,18 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
     if (e != cudaSuccess) return bcuda(e, "launching the batch phases");
     return HC_OK;
 }
+}  // namespace
 
 }  // extern "C"
+
+namespace hc {
+// hc_batch_run for callers that own page-locked staging for the descriptors
+// (the served loop: one buffer per launch slot, reused only after the slot's
+// launch completed), so that their copy to the device does not wait for the
+// stream.
+hc_rc batch_run_pinned(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg, void *d_scratch,
+                       int64_t scratch_bytes, void *h_pinned, void *stream) {
+    return batch_run(items, n_items, cfg, d_scratch, scratch_bytes, h_pinned, stream);
+}
+size_t batch_desc_bytes(int64_t n_items) { return (size_t)n_items * sizeof(BatchItemDev); }
+}  // namespace hc

@@ -53,6 +53,12 @@ cudaError_t ordered_leaders(const void *keys, int key_bytes, long long n, void *
 cudaError_t ordered_follow_insert(long long n, void *scratch, uint8_t *status, int sms, cudaStream_t s);
 const uint8_t *ordered_skip(long long n, const void *scratch);
 
+// hc_batch_run with the descriptors written into caller-owned page-locked
+// staging of batch_desc_bytes(n_items) (hc_batch.cu).
+hc_rc batch_run_pinned(const hc_batch_item *items, int64_t n_items, const hc_batch_config *cfg, void *d_scratch,
+                       int64_t scratch_bytes, void *h_pinned, void *stream);
+size_t batch_desc_bytes(int64_t n_items);
+
 // One free-running launch of per-thread insert / find / erase (hc_mixed.cu).
 cudaError_t mixed_ops(const hc_device_view &dv, const uint8_t *ops, const void *keys, const void *vals, long long n,
                       uint8_t *status, void *vals_out, cudaStream_t s);

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "hc.h"
+#include "hc_internal.h"
 #include "hc_table.h"
 
 hc_rc hc_internal_fail(hc_rc rc, const char *msg);
@@ -48,6 +49,7 @@ struct Slot {
     unsigned char *h_out = nullptr;    // pinned host staging of outputs
     void *desc = nullptr;              // descriptor scratch of hc_batch_run
     int64_t desc_bytes = 0;
+    void *h_desc = nullptr;            // pinned staging of the descriptors (copied without waiting)
     cudaEvent_t done = nullptr;
     bool busy = false;
     int64_t out_begin = 0, out_end = 0;
@@ -76,6 +78,7 @@ void release(hc_server *s) {
         if (sl.desc) cudaFree(sl.desc);
         if (sl.h_in) cudaFreeHost(sl.h_in);
         if (sl.h_out) cudaFreeHost(sl.h_out);
+        if (sl.h_desc) cudaFreeHost(sl.h_desc);
     }
     for (cudaStream_t st : s->streams)
         if (st) cudaStreamDestroy(st);
@@ -149,7 +152,8 @@ hc_rc launch(hc_server *s, Slot &sl, hc_request *reqs, const std::vector<int64_t
     }
     hc_rc rc = HC_OK;
     if (s->merge) {
-        rc = hc_batch_run(sl.items.data(), (int64_t)sl.items.size(), &s->batch, sl.desc, sl.desc_bytes, st);
+        rc = hc::batch_run_pinned(sl.items.data(), (int64_t)sl.items.size(), &s->batch, sl.desc, sl.desc_bytes,
+                                  sl.h_desc, st);
     } else {
         for (const hc_batch_item &it : sl.items) {
             if (it.op == HC_OP_INSERT) rc = hc_insert(it.table, it.d_keys, it.d_vals, it.n, it.d_out, st);
@@ -235,6 +239,8 @@ hc_rc hc_server_create(hc_server **out, hc_table *const *tables, int32_t n_table
         if (e == cudaSuccess) e = cudaMalloc(&sl.desc, (size_t)desc_bytes);
         if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_in, (size_t)s->slot_bytes, cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_out, (size_t)s->slot_bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(&sl.h_desc, hc::batch_desc_bytes(s->max_items) + 256, cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     }
     if (e != cudaSuccess) {
