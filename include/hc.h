@@ -411,7 +411,9 @@ typedef struct hc_batch_config {
                                 4 probes in flight per thread; block <= 256) */
     int32_t block;           /* threads per block (0 = 256)                */
     int32_t blocks_per_sm;   /* persistent grid = SMs x this (0 = auto)    */
-    int32_t tile;            /* keys per tile (0 = auto)                   */
+    int32_t tile;            /* keys per chunk, a multiple of 128 (0 = auto:
+                                128..4096 from the total keys, so that the
+                                chunks can occupy every warp slot)          */
     int32_t use_graph;       /* 1: capture the three phases in a CUDA graph */
 } hc_batch_config;
 

@@ -197,6 +197,25 @@ namespace {
 
 constexpr uint32_t kBatchMagic = 0x48434241u;
 
+// tile 0 in the configuration: keys per chunk chosen from the total work so
+// that the chunks can occupy every warp slot of the GPU (64 per SM): a power
+// of two from 128 to 4096.
+int auto_tile(const hc_batch_item *items, int64_t n_items) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms <= 0) {
+        (void)cudaGetLastError();
+        return 4096;
+    }
+    long long total = 0;
+    for (int64_t i = 0; i < n_items; ++i)
+        if (items[i].n > 0) total += items[i].n;
+    const long long per_slot = total / ((long long)sms * 64);
+    int tile = 128;
+    while (tile < 4096 && (long long)tile * 2 <= per_slot) tile *= 2;
+    return tile;
+}
+
 hc_rc bfail(hc_rc rc, const std::string &msg) { return hc_internal_fail(rc, msg.c_str()); }
 
 hc_rc bcuda(cudaError_t e, const char *what) {
@@ -234,7 +253,7 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
     const int lb = c.lane_bytes;
     const int kpt = c.keys_per_group ? c.keys_per_group : 1;
     const int block = c.block ? c.block : 256;
-    const int tile = c.tile ? c.tile : 4096;
+    const int tile = c.tile ? c.tile : auto_tile(items, n_items);
     if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole bucket) or 32");
     if (kpt != 1 && kpt != 2 && kpt != 4 && kpt != 8)
         return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2 (lock-step) or 4 or 8 (streaming)");
@@ -431,7 +450,7 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
     const int lb = c.lane_bytes;
     const int kpt = c.keys_per_group ? c.keys_per_group : 1;
     const int block = c.block ? c.block : 256;
-    const int tile = c.tile ? c.tile : 4096;
+    const int tile = c.tile ? c.tile : auto_tile(items, n_items);
     if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole bucket) or 32");
     if (kpt != 1 && kpt != 2 && kpt != 4 && kpt != 8)
         return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2 (lock-step) or 4 or 8 (streaming)");
@@ -568,7 +587,7 @@ hc_rc batch_run(const hc_batch_item *items, int64_t n_items, const hc_batch_conf
     const int lb = c.lane_bytes;
     const int kpt = c.keys_per_group ? c.keys_per_group : 1;
     const int block = c.block ? c.block : 256;
-    const int tile = c.tile ? c.tile : 4096;
+    const int tile = c.tile ? c.tile : auto_tile(items, n_items);
     if (lb != 0 && lb != 32) return bfail(HC_ERR_ARG, "lane_bytes must be 0 (whole key region) or 32");
     if (kpt != 1 && kpt != 2 && kpt != 4 && kpt != 8)
         return bfail(HC_ERR_ARG, "keys_per_group must be 1 or 2 (lock-step) or 4 or 8 (streaming)");

@@ -202,7 +202,7 @@ hc_rc hc_server_create(hc_server **out, hc_table *const *tables, int32_t n_table
     if (n_tables < 1 || !tables) return sfail(HC_ERR_ARG, "a server needs at least one table");
     for (int32_t i = 0; i < n_tables; ++i)
         if (!tables[i] || tables[i]->magic != HC_TABLE_MAGIC) return sfail(HC_ERR_ARG, "bad table handle");
-    hc_serve_config c{4, 2, 64ll << 20, 1, 256, {0, 1, 256, 0, 1024, 0}};
+    hc_serve_config c{4, 2, 64ll << 20, 1, 256, {0, 1, 256, 0, 0, 0}};
     if (cfg) {
         if (cfg->lanes) c.lanes = cfg->lanes;
         if (cfg->depth) c.depth = cfg->depth;

@@ -57,7 +57,7 @@ class ServedRequest:
 
 class Server:
     def __init__(self, tables: list[Table], slot_bytes: int = 64 << 20, lanes: int = 4, depth: int = 2,
-                 merge: bool = True, max_items: int = 256, batch_config: tuple = (0, 1, 256, 0, 1024, 0)):
+                 merge: bool = True, max_items: int = 256, batch_config: tuple = (0, 1, 256, 0, 0, 0)):
         self.lib = L.load()
         self.tables = tables
         self.lanes, self.depth, self.merge = lanes, depth, merge
