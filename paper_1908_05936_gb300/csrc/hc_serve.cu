@@ -40,7 +40,18 @@ struct Placed {
     int64_t k_off, v_off;          // device offsets of the inputs (v_off < 0: none)
     int64_t o_off, vo_off;         // device offsets of the outputs (vo_off < 0: none)
     bool packed;                   // inputs copied through the slot's host staging
+    bool direct_out;               // outputs copied straight into the request's page-locked arrays
 };
+
+bool page_locked(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
 
 struct Slot {
     int lane = 0;
@@ -67,6 +78,7 @@ struct hc_server {
     hc_batch_config batch;
     std::vector<cudaStream_t> streams;
     std::vector<Slot> slots;
+    std::vector<bool> out_locked;      // per request of the current run: its outputs are page-locked
 };
 
 namespace {
@@ -104,7 +116,8 @@ hc_rc launch(hc_server *s, Slot &sl, hc_request *reqs, const std::vector<int64_t
         const int kb = key_bytes(kind), vb = val_bytes(kind);
         int64_t in, out;
         need(s, r, &in, &out);
-        Placed p{ri, off, (r.op == HC_OP_INSERT && vb) ? off + round256(r.n * kb) : -1, 0, -1, r.n <= kPackLimit};
+        Placed p{ri, off, (r.op == HC_OP_INSERT && vb) ? off + round256(r.n * kb) : -1, 0, -1, r.n <= kPackLimit,
+                 r.n > kPackLimit && s->out_locked[(size_t)ri]};
         if (p.packed) {
             std::memcpy(sl.h_in + p.k_off, r.h_keys, (size_t)(r.n * kb));
             if (p.v_off >= 0) std::memcpy(sl.h_in + p.v_off, r.h_vals, (size_t)(r.n * vb));
@@ -113,18 +126,24 @@ hc_rc launch(hc_server *s, Slot &sl, hc_request *reqs, const std::vector<int64_t
         sl.placed.push_back(p);
         off += in;
     }
+    // outputs: the ones that go through the host staging first (one copy
+    // back for all of them), then the ones copied straight into page-locked
+    // request arrays
     int64_t o = round256(off);
     sl.out_begin = o;
-    for (Placed &p : sl.placed) {
-        const hc_request &r = reqs[p.req];
-        const int vb = val_bytes(s->tables[r.table]->kind);
-        p.o_off = o;
-        p.vo_off = (r.op == HC_OP_FIND && vb) ? o + round256(r.n) : -1;
-        int64_t in, out;
-        need(s, r, &in, &out);
-        o += out;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (Placed &p : sl.placed) {
+            if (p.direct_out != (pass == 1)) continue;
+            const hc_request &r = reqs[p.req];
+            const int vb = val_bytes(s->tables[r.table]->kind);
+            p.o_off = o;
+            p.vo_off = (r.op == HC_OP_FIND && vb) ? o + round256(r.n) : -1;
+            int64_t in, out;
+            need(s, r, &in, &out);
+            o += out;
+        }
+        if (pass == 0) sl.out_end = o;
     }
-    sl.out_end = o;
     cudaError_t e = cudaSuccess;
     if (packed_end > 0) e = cudaMemcpyAsync(sl.d_buf, sl.h_in, (size_t)packed_end, cudaMemcpyHostToDevice, st);
     for (const Placed &p : sl.placed) {
@@ -163,8 +182,17 @@ hc_rc launch(hc_server *s, Slot &sl, hc_request *reqs, const std::vector<int64_t
         }
     }
     if (rc != HC_OK) return rc;
-    e = cudaMemcpyAsync(sl.h_out + sl.out_begin, sl.d_buf + sl.out_begin, (size_t)(sl.out_end - sl.out_begin),
-                        cudaMemcpyDeviceToHost, st);
+    if (sl.out_end > sl.out_begin)
+        e = cudaMemcpyAsync(sl.h_out + sl.out_begin, sl.d_buf + sl.out_begin, (size_t)(sl.out_end - sl.out_begin),
+                            cudaMemcpyDeviceToHost, st);
+    for (const Placed &p : sl.placed) {
+        if (!p.direct_out || e != cudaSuccess) continue;
+        const hc_request &r = reqs[p.req];
+        if (r.h_status) e = cudaMemcpyAsync(r.h_status, sl.d_buf + p.o_off, (size_t)r.n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && p.vo_off >= 0 && r.h_vals_out)
+            e = cudaMemcpyAsync(r.h_vals_out, sl.d_buf + p.vo_off,
+                                (size_t)(r.n * val_bytes(s->tables[r.table]->kind)), cudaMemcpyDeviceToHost, st);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
     if (e != cudaSuccess) return scuda(e, "copying results to the host");
     sl.busy = true;
@@ -175,8 +203,10 @@ void complete(hc_server *s, Slot &sl, hc_request *reqs, double t_done) {
     for (const Placed &p : sl.placed) {
         hc_request &r = reqs[p.req];
         const int vb = val_bytes(s->tables[r.table]->kind);
-        if (r.h_status) std::memcpy(r.h_status, sl.h_out + p.o_off, (size_t)r.n);
-        if (p.vo_off >= 0 && r.h_vals_out) std::memcpy(r.h_vals_out, sl.h_out + p.vo_off, (size_t)(r.n * vb));
+        if (!p.direct_out) {
+            if (r.h_status) std::memcpy(r.h_status, sl.h_out + p.o_off, (size_t)r.n);
+            if (p.vo_off >= 0 && r.h_vals_out) std::memcpy(r.h_vals_out, sl.h_out + p.vo_off, (size_t)(r.n * vb));
+        }
         r.done = t_done;
     }
     sl.busy = false;
@@ -278,6 +308,13 @@ hc_rc hc_server_run(hc_server *srv, hc_request *reqs, int64_t n_reqs, int32_t re
         need(srv, r, &in, &out);
         if (in + out + 256 > srv->slot_bytes)
             return sfail(HC_ERR_ARG, "request " + std::to_string(i) + " needs more than a launch slot");
+    }
+    srv->out_locked.assign((size_t)n_reqs, false);
+    for (int64_t i = 0; i < n_reqs; ++i) {
+        const hc_request &r = reqs[i];
+        if (r.n <= kPackLimit) continue;
+        const bool vals = r.op == HC_OP_FIND && val_bytes(srv->tables[r.table]->kind) && r.h_vals_out;
+        srv->out_locked[(size_t)i] = (!r.h_status || page_locked(r.h_status)) && (!vals || page_locked(r.h_vals_out));
     }
     // work queued before the run (filling the tables, on any stream) comes first
     const cudaError_t e0 = cudaDeviceSynchronize();
