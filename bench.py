@@ -361,6 +361,7 @@ def run_gpu(args, rank: int, world: int):
         out["config"]["launch"] = {"block": blk}
     else:
         out["other_ops"] = time_rehash_dump(t, torch)
+        out["other_ops"]["ordered_mixed"] = time_ordered_mixed(t, torch, seed=rank)
     if not args.no_e2e and not in_kernel:
         out["e2e"] = run_e2e(t, wl, fill, vals, hit, miss, er, stream)
     t.close()
@@ -414,6 +415,70 @@ def time_rehash_dump(t, torch):
             "select": {"ms": round(sel_ms, 3), "selected": sel, "slots_per_s_g": round(st1["capacity"] / sel_ms / 1e6, 1),
                        "key_gbs": round((key_bytes + sel * 32) / (sel_ms * 1e-3) / 1e9, 1)},
             "size": {"us": round(size_s * 1e6, 1)}}
+
+
+def time_ordered_mixed(t, torch, seed: int = 0) -> dict:
+    """Ordered calls and mixed batches on the table a step left behind
+    (rehashed), against the plain calls on the same keys; CUDA events, median
+    of three repetitions, nothing here inside the step's timed region.
+
+    * ordered insert / erase (the lowest index wins among equal keys, every
+      position gets the sequential result) of 2^24 draws from 2^23 fresh keys,
+      against the plain insert / erase of the same draws;
+    * a free-running mixed batch over the same draws (50 / 30 / 20 insert /
+      find / erase, per position), against the three plain calls of its parts.
+    Every repetition starts from the same table contents: the draws' keys are
+    erased (untimed) after each timed call that inserts them."""
+    from paper_1908_05936_gb300.table import to_device
+    from workloads import recipes, splitmix
+    n, nd = 1 << 24, 1 << 23
+    keys_h = recipes.repeated_keys(n, nd, seed)
+    ops_h = recipes.mixed_ops(n, seed=seed)
+    d_keys, d_vals = to_device(keys_h), to_device(splitmix.value_of(keys_h))
+    d_ops = torch.from_numpy(ops_h).cuda()
+    d_parts = [to_device(keys_h[ops_h == k]) for k in range(3)]
+    d_part_vals = to_device(splitmix.value_of(keys_h[ops_h == 0]))
+    st = torch.empty(n, dtype=torch.uint8, device="cuda")
+    vo = torch.empty(n, dtype=torch.int64, device="cuda")
+    scratch = torch.empty(int(t.lib.hc_ordered_scratch_bytes(n)) + 256, dtype=torch.uint8, device="cuda")
+    live0 = t.size()
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def reset():
+        t.erase(d_keys, status=False)
+        torch.cuda.synchronize()
+
+    res = {k: [] for k in ("insert", "insert_ordered", "erase", "erase_ordered", "mixed", "parts")}
+    for _ in range(4):
+        res["insert"].append(timed(lambda: t.insert(d_keys, d_vals, status=st)))
+        res["erase"].append(timed(lambda: t.erase(d_keys, status=st)))
+        res["insert_ordered"].append(timed(lambda: t.insert_ordered(d_keys, d_vals, status=st, scratch=scratch)))
+        res["erase_ordered"].append(timed(lambda: t.erase_ordered(d_keys, status=st, scratch=scratch)))
+        res["mixed"].append(timed(lambda: t.apply_mixed(d_ops, d_keys, d_vals, status=st, vals_out=vo)))
+        reset()
+
+        def parts():
+            t.insert(d_parts[0], d_part_vals, status=st)
+            t.find(d_parts[1], found=st, vals_out=vo)
+            t.erase(d_parts[2], status=st)
+        res["parts"].append(timed(parts))
+        reset()
+    assert t.size() == live0
+    med = {k: float(np.median(v[1:])) for k, v in res.items()}        # the first repetition warms up
+    rate = lambda ms: round(n / (ms * 1e-3) / 1e6, 1)
+    return {"keys": n, "distinct": nd, "mix": [0.5, 0.3, 0.2],
+            **{k: {"ms": round(v, 3), "mops": rate(v)} for k, v in med.items()},
+            "ordered_over_plain": {"insert": round(med["insert_ordered"] / med["insert"], 2),
+                                   "erase": round(med["erase_ordered"] / med["erase"], 2)},
+            "mixed_over_parts": round(med["mixed"] / med["parts"], 2)}
 
 
 def run_e2e(t, wl, fill, vals, hit, miss, er, stream):

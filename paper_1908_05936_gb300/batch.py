@@ -32,9 +32,14 @@ class Batch:
         self.items = list(items)          # keeps every tensor alive while the batch exists
         arr = (L.BatchItem * max(1, len(self.items)))()
         for i, it in enumerate(self.items):
+            n = it.keys.numel()
             _check_tensor(it.keys, it.table.key_bytes, "keys")
+            if it.vals is not None and it.table.is_map:
+                _check_tensor(it.vals, it.table.val_bytes, "vals", n)
             if it.out is not None:
-                _check_tensor(it.out, 1, "out")
+                _check_tensor(it.out, 1, "out", n)
+            if it.vals_out is not None and it.table.is_map:
+                _check_tensor(it.vals_out, it.table.val_bytes, "vals_out", n)
             arr[i] = L.BatchItem(it.table.handle, it.op, 0, it.keys.data_ptr(),
                                  it.vals.data_ptr() if it.vals is not None else None, it.keys.numel(),
                                  it.out.data_ptr() if it.out is not None else None,

@@ -14,20 +14,46 @@ namespace hc {
 
 namespace {
 
+constexpr int kMixedBlock = 256;
+
+// One block takes kMixedBlock consecutive positions and hands them to its
+// threads grouped by operation kind (inserts, then finds, then erases), so a
+// warp runs one kind's code path instead of all three one after another.
+// The call implies no order across positions, so any assignment of positions
+// to threads is a valid schedule.
 template <int KIND>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kMixedBlock)
 k_mixed(hc_device_view dv, const uint8_t *ops, const typename Traits<KIND>::Key *keys,
         const typename Traits<KIND>::Val *vals, long long n, uint8_t *status, typename Traits<KIND>::Val *vals_out) {
     using Tab = hcd::Table<KIND>;
+    __shared__ unsigned s_count[3];
+    __shared__ unsigned s_pos[kMixedBlock];    // tile offset | kind << 16, grouped by kind
+    const long long base = (long long)blockIdx.x * kMixedBlock;
+    const int tid = threadIdx.x;
+    if (tid < 3) s_count[tid] = 0;
+    __syncthreads();
+    int kind = -1;
+    unsigned slot = 0;
+    if (base + tid < n) {
+        const uint8_t op = __ldcs(ops + base + tid);
+        kind = op == OP_INSERT ? 0 : (op == OP_FIND ? 1 : 2);
+        slot = atomicAdd(&s_count[kind], 1u);
+    }
+    __syncthreads();
+    if (kind >= 0) {
+        const unsigned off = kind == 0 ? 0u : (kind == 1 ? s_count[0] : s_count[0] + s_count[1]);
+        s_pos[off + slot] = (unsigned)tid | ((unsigned)kind << 16);
+    }
+    __syncthreads();
+    if ((unsigned)tid >= s_count[0] + s_count[1] + s_count[2]) return;
+    const unsigned e = s_pos[tid];
+    const long long i = base + (e & 0xFFFFu);
     const Tab t(dv);
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint8_t op = __ldcs(ops + i);
     const typename Tab::Key k = __ldcs(keys + i);
     uint8_t st;
-    if (op == OP_INSERT) {
+    if ((e >> 16) == 0) {
         st = (uint8_t)t.insert(k, (Tab::is_map && vals) ? __ldcs(vals + i) : typename Tab::Val()).status;
-    } else if (op == OP_FIND) {
+    } else if ((e >> 16) == 1) {
         const long long pos = t.find(k);
         st = pos != hcd::END;
         if constexpr (Tab::is_map) {
@@ -43,8 +69,7 @@ template <int KIND>
 cudaError_t launch(const hc_device_view &dv, const uint8_t *ops, const void *keys, const void *vals, long long n,
                    uint8_t *status, void *vals_out, cudaStream_t s) {
     using T = Traits<KIND>;
-    const int block = 128;
-    k_mixed<KIND><<<(unsigned)((n + block - 1) / block), block, 0, s>>>(
+    k_mixed<KIND><<<(unsigned)((n + kMixedBlock - 1) / kMixedBlock), kMixedBlock, 0, s>>>(
         dv, ops, (const typename T::Key *)keys, (const typename T::Val *)vals, n, status,
         (typename T::Val *)vals_out);
     return cudaGetLastError();

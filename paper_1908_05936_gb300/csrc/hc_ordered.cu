@@ -30,8 +30,8 @@ __device__ __forceinline__ unsigned long long aux_hash(unsigned long long k) {
 template <class Key>
 __global__ void __launch_bounds__(256) k_claim_leaders(const Key *keys, long long n, long long *aux,
                                                        unsigned long long mask, unsigned *err) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
         const Key k = keys[i];
         unsigned long long h = aux_hash((unsigned long long)k) & mask;
         bool done = false;
@@ -56,8 +56,8 @@ __global__ void __launch_bounds__(256) k_claim_leaders(const Key *keys, long lon
 template <class Key>
 __global__ void __launch_bounds__(256) k_mark_followers(const Key *keys, long long n, const long long *aux,
                                                         unsigned long long mask, long long *lead, uint8_t *skip) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
         const Key k = keys[i];
         unsigned long long h = aux_hash((unsigned long long)k) & mask;
         long long leader = i;
@@ -77,14 +77,15 @@ __global__ void __launch_bounds__(256) k_mark_followers(const Key *keys, long lo
 
 __global__ void __launch_bounds__(256) k_follow_insert(long long n, const long long *lead, const uint8_t *skip,
                                                        uint8_t *status) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        if (skip[i]) status[i] = status[lead[i]] == ST_OVERFLOW ? (uint8_t)ST_OVERFLOW : (uint8_t)ST_EXISTS;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && skip[i]) status[i] = status[lead[i]] == ST_OVERFLOW ? (uint8_t)ST_OVERFLOW : (uint8_t)ST_EXISTS;
 }
 
-unsigned grid_of(long long n, int sms) {
+// One thread per key and as many 256-thread blocks as the keys need: short
+// blocks let an SM refill as soon as its slowest probes finish.
+unsigned grid_of(long long n, int) {
     const long long g = (n + 255) / 256;
-    return (unsigned)(g < (long long)sms * 8 ? (g > 0 ? g : 1) : (long long)sms * 8);
+    return (unsigned)(g > 0 ? g : 1);
 }
 
 }  // namespace

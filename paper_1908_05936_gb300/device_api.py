@@ -56,20 +56,25 @@ def apply(table: Table, keys: torch.Tensor, op: int | torch.Tensor = L.OP_INSERT
     ops = None
     op_all = 0
     if isinstance(op, torch.Tensor):
-        _check_tensor(op, 1, "ops")
+        _check_tensor(op, 1, "ops", n)
         ops = op
     else:
         op_all = int(op)
     if status is None:
         status = torch.empty(n, dtype=torch.uint8, device=keys.device)
+    _check_tensor(status, 1, "status", n)
     if vals is not None:
-        _check_tensor(vals, table.val_bytes, "vals")
+        _check_tensor(vals, table.val_bytes, "vals", n)
     if vals_out is True:
         vals_out = torch.empty(n, dtype=torch.int32 if table.val_bytes == 4 else torch.int64, device=keys.device)
     if pos_out is True:
         pos_out = torch.empty(n, dtype=torch.int64, device=keys.device)
     vo = vals_out if isinstance(vals_out, torch.Tensor) else None
     po = pos_out if isinstance(pos_out, torch.Tensor) else None
+    if vo is not None:
+        _check_tensor(vo, table.val_bytes, "vals_out", n)
+    if po is not None:
+        _check_tensor(po, 8, "pos_out", n)
     _rc(ex.hcx_apply(ctypes.byref(dv), ops.data_ptr() if ops is not None else None, op_all, keys.data_ptr(),
                      vals.data_ptr() if vals is not None else None, n, status.data_ptr(),
                      vo.data_ptr() if vo is not None else None, po.data_ptr() if po is not None else None, block,

@@ -45,11 +45,16 @@ def to_numpy(t: torch.Tensor, dtype) -> np.ndarray:
     return t.detach().cpu().numpy().view(dtype)
 
 
-def _check_tensor(t: torch.Tensor, nbytes: int, name: str):
+def _check_tensor(t: torch.Tensor, nbytes: int, name: str, n: int | None = None):
+    """A CUDA tensor, contiguous, with `nbytes`-byte elements and (when `n`
+    is given) room for at least n of them: the kernels write outputs by
+    index, so a short buffer is refused here."""
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.element_size() != nbytes or not t.is_contiguous():
         raise TypeError(f"{name} must be contiguous with {nbytes}-byte elements")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, {n} needed")
 
 
 def pack_short3(xyz: torch.Tensor, stream=None) -> torch.Tensor:
@@ -136,7 +141,7 @@ class Table:
         elif status is False:
             status = None
         if status is not None:
-            _check_tensor(status, 1, "status")
+            _check_tensor(status, 1, "status", n)
         L.check(self.lib.hc_insert(self.h, keys.data_ptr(), vals.data_ptr() if self.is_map else None, n,
                                    status.data_ptr() if status is not None else None, _stream_handle(stream)))
         return status
@@ -146,14 +151,16 @@ class Table:
         """Insert the keys whose ``found`` flag (from ``find`` on the same keys)
         is 0; flagged keys get EXISTS without a probe."""
         _check_tensor(keys, self.key_bytes, "keys")
-        _check_tensor(found, 1, "found")
         n = keys.numel()
+        _check_tensor(found, 1, "found", n)
         if self.is_map:
-            _check_tensor(vals, self.val_bytes, "vals")
+            _check_tensor(vals, self.val_bytes, "vals", n)
         if status is True:
             status = torch.empty(n, dtype=torch.uint8, device=keys.device)
         elif status is False:
             status = None
+        if status is not None:
+            _check_tensor(status, 1, "status", n)
         L.check(self.lib.hc_insert_if_absent(self.h, keys.data_ptr(), vals.data_ptr() if self.is_map else None,
                                              found.data_ptr(), n, status.data_ptr() if status is not None else None,
                                              _stream_handle(stream)))
@@ -169,15 +176,19 @@ class Table:
         if ops.numel() != n:
             raise ValueError("ops and keys differ in length")
         if self.is_map:
-            _check_tensor(vals, self.val_bytes, "vals")
+            _check_tensor(vals, self.val_bytes, "vals", n)
         if status is True:
             status = torch.empty(n, dtype=torch.uint8, device=keys.device)
         elif status is False:
             status = None
+        if status is not None:
+            _check_tensor(status, 1, "status", n)
         if self.is_map and vals_out is True:
             vals_out = torch.empty(n, dtype=KEY_TORCH[self.val_bytes], device=keys.device)
         elif not isinstance(vals_out, torch.Tensor) or not self.is_map:
             vals_out = None
+        if vals_out is not None:
+            _check_tensor(vals_out, self.val_bytes, "vals_out", n)
         L.check(self.lib.hc_apply_mixed(self.h, ops.data_ptr(), keys.data_ptr(),
                                         vals.data_ptr() if self.is_map else None, n,
                                         status.data_ptr() if status is not None else None,
@@ -186,7 +197,7 @@ class Table:
 
     def _scratch(self, n: int, scratch: torch.Tensor | None) -> torch.Tensor:
         need = int(self.lib.hc_ordered_scratch_bytes(n))
-        if scratch is None or scratch.numel() < need:
+        if scratch is None or scratch.numel() < need + 255:     # room to align the base to 256 bytes
             scratch = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
         return scratch
 
@@ -197,11 +208,13 @@ class Table:
         _check_tensor(keys, self.key_bytes, "keys")
         n = keys.numel()
         if self.is_map:
-            _check_tensor(vals, self.val_bytes, "vals")
+            _check_tensor(vals, self.val_bytes, "vals", n)
         if status is True:
             status = torch.empty(n, dtype=torch.uint8, device=keys.device)
         elif status is False:
             status = None
+        if status is not None:
+            _check_tensor(status, 1, "status", n)
         sc = self._scratch(n, scratch)
         base = (sc.data_ptr() + 255) // 256 * 256
         L.check(self.lib.hc_insert_ordered(self.h, keys.data_ptr(), vals.data_ptr() if self.is_map else None, n,
@@ -219,6 +232,8 @@ class Table:
             status = torch.empty(n, dtype=torch.uint8, device=keys.device)
         elif status is False:
             status = None
+        if status is not None:
+            _check_tensor(status, 1, "status", n)
         sc = self._scratch(n, scratch)
         base = (sc.data_ptr() + 255) // 256 * 256
         L.check(self.lib.hc_erase_ordered(self.h, keys.data_ptr(), n, status.data_ptr() if status is not None else None,
@@ -231,13 +246,13 @@ class Table:
         n = keys.numel()
         if found is None:
             found = torch.empty(n, dtype=torch.uint8, device=keys.device)
-        _check_tensor(found, 1, "found")
+        _check_tensor(found, 1, "found", n)
         if self.is_map and vals_out is True:
             vals_out = torch.empty(n, dtype=KEY_TORCH[self.val_bytes], device=keys.device)
         elif vals_out is True or vals_out is False or not self.is_map:
             vals_out = None
         if vals_out is not None:
-            _check_tensor(vals_out, self.val_bytes, "vals_out")
+            _check_tensor(vals_out, self.val_bytes, "vals_out", n)
         L.check(self.lib.hc_find(self.h, keys.data_ptr(), n, found.data_ptr(),
                                  vals_out.data_ptr() if vals_out is not None else None, _stream_handle(stream)))
         return found, vals_out
@@ -250,7 +265,7 @@ class Table:
         elif status is False:
             status = None
         if status is not None:
-            _check_tensor(status, 1, "status")
+            _check_tensor(status, 1, "status", n)
         L.check(self.lib.hc_erase(self.h, keys.data_ptr(), n, status.data_ptr() if status is not None else None,
                                   _stream_handle(stream)))
         return status
@@ -262,14 +277,29 @@ class Table:
             raise TypeError(f"host array must have {nbytes}-byte elements")
         return a
 
+    @staticmethod
+    def _host_out(a: np.ndarray, nbytes: int, n: int, name: str) -> np.ndarray:
+        """An output array the library writes in place: C-contiguous,
+        writeable, `nbytes`-byte elements, at least n of them."""
+        if not isinstance(a, np.ndarray) or not a.flags.c_contiguous or not a.flags.writeable:
+            raise TypeError(f"{name} must be a writeable C-contiguous numpy array")
+        if a.dtype.itemsize != nbytes:
+            raise TypeError(f"{name} must have {nbytes}-byte elements")
+        if a.size < n:
+            raise ValueError(f"{name} holds {a.size} elements, {n} needed")
+        return a
+
     def insert_host(self, keys: np.ndarray, vals: np.ndarray | None = None, status: np.ndarray | None = None,
                     stream=None) -> np.ndarray:
         keys = self._host(keys, self.key_bytes)
         n = len(keys)
         if self.is_map:
             vals = self._host(vals, self.val_bytes)
+            if len(vals) != n:
+                raise ValueError("keys and vals differ in length")
         if status is None:
             status = np.empty(n, np.uint8)
+        self._host_out(status, 1, n, "status")
         L.check(self.lib.hc_insert_host(self.h, keys.ctypes.data, vals.ctypes.data if self.is_map else None, n,
                                         status.ctypes.data, _stream_handle(stream)))
         return status
@@ -282,6 +312,9 @@ class Table:
             found = np.empty(n, np.uint8)
         if self.is_map and vals_out is None:
             vals_out = np.empty(n, VAL_NUMPY[self.kind])
+        self._host_out(found, 1, n, "found")
+        if self.is_map:
+            self._host_out(vals_out, self.val_bytes, n, "vals_out")
         L.check(self.lib.hc_find_host(self.h, keys.ctypes.data, n, found.ctypes.data,
                                       vals_out.ctypes.data if self.is_map else None, _stream_handle(stream)))
         return found, (vals_out if self.is_map else None)
@@ -291,6 +324,7 @@ class Table:
         n = len(keys)
         if status is None:
             status = np.empty(n, np.uint8)
+        self._host_out(status, 1, n, "status")
         L.check(self.lib.hc_erase_host(self.h, keys.ctypes.data, n, status.ctypes.data, _stream_handle(stream)))
         return status
 
@@ -312,7 +346,10 @@ class Table:
             vals_out = None
         if count is None:
             count = torch.zeros(1, dtype=torch.int64, device=self.device)
-        _check_tensor(count, 8, "count")
+        _check_tensor(count, 8, "count", 1)
+        _check_tensor(keys_out, self.key_bytes, "keys_out", cap)
+        if vals_out is not None:
+            _check_tensor(vals_out, self.val_bytes, "vals_out", cap)
         wrap = lambda x: ((int(x) + 2**63) % 2**64) - 2**63
         pred = L.Predicate(kind, int(negate), wrap(lo), wrap(hi), (ctypes.c_int32 * 6)(*box))
         L.check(self.lib.hc_select(self.h, ctypes.byref(pred), keys_out.data_ptr(),

@@ -393,3 +393,40 @@ def test_tombstone_reuse_keeps_keys_unique(kind):
             assert p.g.size() == min(4, len(set(C.bits(keys).tolist())))
         finally:
             p.close()
+
+
+def test_binding_refuses_short_buffers():
+    """The kernels write outputs by index, so the binding refuses an output
+    (or a value array) shorter than the key array before any launch, and the
+    table is left untouched."""
+    from paper_1908_05936_gb300.table import Table
+    t = Table(O.MAP_U64_U64, 1000)
+    try:
+        k = to_device(np.arange(1, 101, dtype=np.uint64))
+        v = to_device(np.arange(1, 101, dtype=np.uint64))
+        short8 = torch.empty(99, dtype=torch.int64, device="cuda")
+        short1 = torch.empty(99, dtype=torch.uint8, device="cuda")
+        with pytest.raises(ValueError):
+            t.insert(k, v, status=short1)
+        with pytest.raises(ValueError):
+            t.insert(k, short8)
+        with pytest.raises(ValueError):
+            t.find(k, found=short1)
+        with pytest.raises(ValueError):
+            t.find(k, vals_out=short8)
+        with pytest.raises(ValueError):
+            t.erase(k, status=short1)
+        with pytest.raises(ValueError):
+            t.insert_ordered(k, v, status=short1)
+        with pytest.raises(ValueError):
+            t.apply_mixed(torch.zeros(100, dtype=torch.uint8, device="cuda"), k, v, vals_out=short8)
+        with pytest.raises(ValueError):
+            t.select(keys_out=short8, cap=100)
+        with pytest.raises(ValueError):
+            t.find_host(np.arange(100, dtype=np.uint64), found=np.empty(99, np.uint8))
+        assert t.size() == 0
+        t.insert(k, v)
+        f, vo = t.find(k)
+        assert to_numpy(f, np.uint8).all() and np.array_equal(to_numpy(vo, np.uint64), np.arange(1, 101))
+    finally:
+        t.close()

@@ -9,6 +9,7 @@ Every array here is drawn from counter-based splitmix64 streams
   10..19     permutations and samples
   1000 + t   multi-table workload, table t (inserts), 5000 + t (fresh finds)
   3000..     served workload (arrivals, sizes, ops, ranks)
+  40..42     batches with repeated keys: the key domain, draws, op kinds
 """
 from __future__ import annotations
 
@@ -76,6 +77,22 @@ def map_hit_keys(n_inserted: int, n: int, seed: int = 0, salt: int = 0) -> np.nd
 def map_miss_keys(n: int, seed: int = 0, start: int = 0) -> np.ndarray:
     """Fresh keys (stream 4): absent unless a 2^-64-per-pair collision hits."""
     return sm.stream_u64(4, seed, start, n)
+
+
+def repeated_keys(n: int, n_distinct: int, seed: int = 0) -> np.ndarray:
+    """n draws, uniform with replacement, from n_distinct fresh uint64 keys
+    (stream 40 holds the domain, stream 41 the draws): each key appears
+    n / n_distinct times on average, in scattered positions."""
+    u = sm.uniform01(41, seed, 0, n)
+    idx = np.minimum((u * n_distinct).astype(np.int64), n_distinct - 1)
+    return sm.stream_at(40, seed, idx)
+
+
+def mixed_ops(n: int, mix=(0.5, 0.3, 0.2), seed: int = 0) -> np.ndarray:
+    """Op kinds of a mixed batch (0 insert, 1 find, 2 erase) drawn
+    independently per position with probabilities `mix` (stream 42)."""
+    u = sm.uniform01(42, seed, 0, n)
+    return np.where(u < mix[0], 0, np.where(u < mix[0] + mix[1], 1, 2)).astype(np.uint8)
 
 
 # ---------------------------------------------------------------------------
