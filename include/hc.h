@@ -283,7 +283,7 @@ HC_API hc_rc hc_apply_mixed(hc_table *t, const uint8_t *d_ops, const void *d_key
  *
  * d_scratch: device memory of hc_ordered_scratch_bytes(n) bytes, 256-byte
  * aligned, owned by the caller, free for reuse once the call's work on
- * `stream` is done (about 16 bytes per key, plus n bytes).  Asynchronous.
+ * `stream` is done (32 to 64 bytes per key, plus 9n bytes).  Asynchronous.
  * HC_ERR_ARG if the scratch is NULL, misaligned or too small. */
 HC_API int64_t hc_ordered_scratch_bytes(int64_t n);
 HC_API hc_rc hc_insert_ordered(hc_table *t, const void *d_keys, const void *d_vals, int64_t n, uint8_t *d_status,

@@ -573,8 +573,7 @@ hc_rc hc_dump(hc_table *t, void *d_keys_out, void *d_vals_out, int64_t cap, int6
 
 int64_t hc_ordered_scratch_bytes(int64_t n) {
     if (n < 0) return -1;
-    const unsigned long long P = hc::ordered_aux_slots(n);
-    return (int64_t)(((P + (unsigned long long)n) * 8ull + (unsigned long long)n + 255ull) / 256ull * 256ull);
+    return (int64_t)hc::ordered_scratch_bytes(n);
 }
 
 static hc_rc ordered_checks(const hc_table *t, int op, const void *keys, const void *vals, long long n,

@@ -48,6 +48,7 @@ struct SelectPred {
 
 // Ordered calls (hc_ordered.cu): scratch layout and the leader passes.
 unsigned long long ordered_aux_slots(long long n);
+long long ordered_scratch_bytes(long long n);
 cudaError_t ordered_leaders(const void *keys, int key_bytes, long long n, void *scratch, unsigned *err, int sms,
                             cudaStream_t s);
 cudaError_t ordered_follow_insert(long long n, void *scratch, uint8_t *status, int sms, cudaStream_t s);

@@ -9,11 +9,14 @@
 // leader's insert (OVERFLOW if the leader overflowed), NOT_FOUND after their
 // leader's erase.
 //
-// Scratch: `aux`, a power of two P >= 2n of int64 indices (-1 = empty slot),
-// probed linearly from a hash of the key; an entry's key is the key at its
-// index in the caller's array, so entries need no key field and a slot's key
-// never changes (atomicMin replaces an index only by a smaller index of the
-// same key).  Then `lead` (n int64 leader indices) and `skip` (n bytes).
+// Scratch: `aux`, a power of two P >= 2n of 16-byte entries (key bits,
+// index), probed linearly from a hash of the key.  An empty entry is all ones
+// (index -1); a claimed entry's index is >= 0, so no claimed entry looks
+// empty, whatever its key.  A key claims an empty entry with one 16-byte
+// compare-and-swap that writes key and index together, so a probe compares
+// keys without reading the caller's array again, and a later occurrence
+// lowers the index with atomicMin (an entry's key never changes).  Then
+// `lead` (n int64 leader indices) and `skip` (n bytes).
 #include <cstdint>
 
 #include "hc_core.cuh"
@@ -27,23 +30,51 @@ __device__ __forceinline__ unsigned long long aux_hash(unsigned long long k) {
     return fmix64(k ^ 0xD6E8FEB86659FD93ull);
 }
 
+struct AuxEntry {
+    unsigned long long key;
+    long long idx;
+};
+
+__device__ __forceinline__ AuxEntry load_entry(const AuxEntry *e) {
+    AuxEntry r;
+    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(r.key), "=l"(r.idx) : "l"(e));
+    return r;
+}
+
+// 16-byte compare-and-swap of an empty entry (all ones) to (key, idx);
+// returns the entry as it was.
+__device__ __forceinline__ AuxEntry claim_entry(AuxEntry *e, unsigned long long key, long long idx) {
+    AuxEntry r;
+    asm volatile("{\n\t.reg .b128 c, v, d;\n\t"
+                 "mov.b128 c, {%2, %2};\n\t"
+                 "mov.b128 v, {%3, %4};\n\t"
+                 "atom.global.cas.b128 d, [%5], c, v;\n\t"
+                 "mov.b128 {%0, %1}, d;\n\t}"
+                 : "=l"(r.key), "=l"(r.idx)
+                 : "l"(~0ull), "l"(key), "l"(idx), "l"(e)
+                 : "memory");
+    return r;
+}
+
 template <class Key>
-__global__ void __launch_bounds__(256) k_claim_leaders(const Key *keys, long long n, long long *aux,
+__global__ void __launch_bounds__(256) k_claim_leaders(const Key *keys, long long n, AuxEntry *aux,
                                                        unsigned long long mask, unsigned *err) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        const Key k = keys[i];
-        unsigned long long h = aux_hash((unsigned long long)k) & mask;
+        const unsigned long long k = (unsigned long long)keys[i];
+        unsigned long long h = aux_hash(k) & mask;
         bool done = false;
         for (unsigned long long p = 0; p <= mask && !done; ++p) {
-            long long cur = *((volatile long long *)&aux[h]);
-            if (cur < 0) {
-                cur = (long long)atomicCAS(reinterpret_cast<unsigned long long *>(&aux[h]), ~0ull,
-                                           (unsigned long long)i);
-                if (cur < 0) { done = true; break; }
+            AuxEntry cur = load_entry(aux + h);
+            // an empty entry is claimed; an entry whose key reads as all ones
+            // goes through the swap too, which returns it whole (a read that
+            // overlapped a claim could pair the new index with the old key)
+            if (cur.idx < 0 || cur.key == ~0ull) {
+                cur = claim_entry(aux + h, k, i);
+                if (cur.idx < 0) { done = true; break; }
             }
-            if (keys[cur] == k) {
-                atomicMin(&aux[h], i);
+            if (cur.key == k) {
+                if (i < cur.idx) atomicMin(&aux[h].idx, i);
                 done = true;
                 break;
             }
@@ -54,18 +85,18 @@ __global__ void __launch_bounds__(256) k_claim_leaders(const Key *keys, long lon
 }
 
 template <class Key>
-__global__ void __launch_bounds__(256) k_mark_followers(const Key *keys, long long n, const long long *aux,
+__global__ void __launch_bounds__(256) k_mark_followers(const Key *keys, long long n, const AuxEntry *aux,
                                                         unsigned long long mask, long long *lead, uint8_t *skip) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        const Key k = keys[i];
-        unsigned long long h = aux_hash((unsigned long long)k) & mask;
+        const unsigned long long k = (unsigned long long)keys[i];
+        unsigned long long h = aux_hash(k) & mask;
         long long leader = i;
         for (unsigned long long p = 0; p <= mask; ++p) {
-            const long long cur = aux[h];
-            if (cur < 0) break;                         // cannot happen: the key was claimed
-            if (keys[cur] == k) {
-                leader = cur;
+            const AuxEntry cur = load_entry(aux + h);
+            if (cur.idx < 0) break;                     // cannot happen: the key was claimed
+            if (cur.key == k) {
+                leader = cur.idx;
                 break;
             }
             h = (h + 1) & mask;
@@ -96,13 +127,18 @@ unsigned long long ordered_aux_slots(long long n) {
     return p;
 }
 
+long long ordered_scratch_bytes(long long n) {
+    const unsigned long long P = ordered_aux_slots(n);
+    return (long long)((P * sizeof(AuxEntry) + (unsigned long long)n * 9ull + 255ull) / 256ull * 256ull);
+}
+
 cudaError_t ordered_leaders(const void *keys, int key_bytes, long long n, void *scratch, unsigned *err, int sms,
                             cudaStream_t s) {
     const unsigned long long P = ordered_aux_slots(n);
-    long long *aux = static_cast<long long *>(scratch);
-    long long *lead = aux + P;
+    AuxEntry *aux = static_cast<AuxEntry *>(scratch);
+    long long *lead = reinterpret_cast<long long *>(aux + P);
     uint8_t *skip = reinterpret_cast<uint8_t *>(lead + n);
-    cudaError_t e = cudaMemsetAsync(aux, 0xFF, P * sizeof(long long), s);
+    cudaError_t e = cudaMemsetAsync(aux, 0xFF, P * sizeof(AuxEntry), s);
     if (e != cudaSuccess) return e;
     const unsigned g = grid_of(n, sms);
     if (key_bytes == 4) {
@@ -118,7 +154,7 @@ cudaError_t ordered_leaders(const void *keys, int key_bytes, long long n, void *
 
 cudaError_t ordered_follow_insert(long long n, void *scratch, uint8_t *status, int sms, cudaStream_t s) {
     const unsigned long long P = ordered_aux_slots(n);
-    const long long *lead = static_cast<const long long *>(scratch) + P;
+    const long long *lead = reinterpret_cast<const long long *>(static_cast<const AuxEntry *>(scratch) + P);
     const uint8_t *skip = reinterpret_cast<const uint8_t *>(lead + n);
     k_follow_insert<<<grid_of(n, sms), 256, 0, s>>>(n, lead, skip, status);
     return cudaGetLastError();
@@ -126,7 +162,7 @@ cudaError_t ordered_follow_insert(long long n, void *scratch, uint8_t *status, i
 
 const uint8_t *ordered_skip(long long n, const void *scratch) {
     const unsigned long long P = ordered_aux_slots(n);
-    return reinterpret_cast<const uint8_t *>(static_cast<const long long *>(scratch) + P + n);
+    return reinterpret_cast<const uint8_t *>(reinterpret_cast<const long long *>(static_cast<const AuxEntry *>(scratch) + P) + n);
 }
 
 }  // namespace hc

@@ -52,7 +52,7 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.hc_destroy(None) == L.OK
     assert lib.hc_batch_create(None, None, 0, None, None) == L.ERR_ARG
     assert lib.hc_ordered_scratch_bytes(-1) == -1
-    assert lib.hc_ordered_scratch_bytes(1000) >= 2048 * 8 + 1000 * 9
+    assert lib.hc_ordered_scratch_bytes(1000) >= 2048 * 16 + 1000 * 9      # 16-byte entries, leaders, skip flags
     assert lib.hc_insert_ordered(None, None, None, 1, None, None, 0, None) == L.ERR_ARG
     assert lib.hc_erase_ordered(None, None, 1, None, None, 0, None) == L.ERR_ARG
     assert lib.hc_apply_mixed(None, None, None, None, 1, None, None, None) == L.ERR_ARG
