@@ -83,7 +83,8 @@ def parse():
     ap.add_argument("--rgbd-hash", type=int, default=1,
                     help="1 = the paper's spatial hash on packed 21-bit coordinates, 2 = on short3 keys, 0 = mix64")
     ap.add_argument("--tables", type=int, default=1024)
-    ap.add_argument("--tile", type=int, default=4096)
+    ap.add_argument("--tile", type=int, default=None,
+                    help="multi_table: keys per chunk (0 = auto); no shape option = the tuned batched shape")
     ap.add_argument("--requests", type=int, default=3000)
     ap.add_argument("--served-tables", type=int, default=64)
     ap.add_argument("--served-slots", type=int, default=56_000_000)
@@ -603,7 +604,15 @@ def run_multi_table(args):
     slots = recipes.multi_table_slots(n_tables)
     ops = [recipes.multi_table_ops(int(s), t) for t, s in enumerate(slots)]
     n_ops = sum(len(o.insert_keys) + len(o.find_keys) + len(o.erase_keys) for o in ops)
-    bb = args.bucket_bytes or 128
+    from paper_1908_05936_gb300 import tune
+    shape = None
+    if not (args.bucket_bytes or args.lane_bytes or args.kpt or args.block or args.tile is not None):
+        shape = tune.batch_config()                   # the autotuner's choice on this GPU, if cached
+    source = "tuned (tune.py --batch)" if shape else "arguments"
+    if shape is None:
+        shape = dict(bucket_bytes=args.bucket_bytes or 128, lane_bytes=args.lane_bytes, keys_per_group=args.kpt,
+                     block=args.block, tile=args.tile if args.tile is not None else 4096)
+    bb = shape["bucket_bytes"]
     arms = {}
     for arm in ("plain", "batched"):
         tabs = [Table(L.SET_U64, int(s), bucket_bytes=bb) for s in slots]
@@ -613,8 +622,8 @@ def run_multi_table(args):
             items += [Item(t, L.OP_INSERT, ki, None, torch.empty(ki.numel(), dtype=torch.uint8, device="cuda")),
                       Item(t, L.OP_FIND, kf, None, torch.empty(kf.numel(), dtype=torch.uint8, device="cuda")),
                       Item(t, L.OP_ERASE, ke, None, torch.empty(ke.numel(), dtype=torch.uint8, device="cuda"))]
-        batch = Batch(items, keys_per_group=args.kpt, block=args.block, tile=args.tile, use_graph=True) \
-            if arm == "batched" else None
+        batch = Batch(items, lane_bytes=shape["lane_bytes"], keys_per_group=shape["keys_per_group"],
+                      block=shape["block"], tile=shape["tile"], use_graph=True) if arm == "batched" else None
         stream = torch.cuda.current_stream()
 
         def step():
@@ -660,7 +669,7 @@ def run_multi_table(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded splitmix64 keys)",
             "config": {"workload": f"{n_tables} set<u64> tables, capacities round(2^U(10,22)), 0.5 x capacity ops "
                                    "60/30/10 insert/find/erase", "total_slots": int(slots.sum()), "ops_per_step": n_ops,
-                       "bucket_bytes": bb, "tile": args.tile},
+                       "bucket_bytes": bb, "batch_shape": dict(shape, source=source)},
             "plain": arms["plain"], "batched": arms["batched"],
             "speedup": round(arms["plain"]["ms_per_step"] / arms["batched"]["ms_per_step"], 3),
             "gpu_launches": arms["batched"]["launches_per_step"] * args.steps}

@@ -412,7 +412,7 @@ typedef struct hc_batch_config {
     int32_t block;           /* threads per block (0 = 256)                */
     int32_t blocks_per_sm;   /* persistent grid = SMs x this (0 = auto)    */
     int32_t tile;            /* keys per chunk, a multiple of 128 (0 = auto:
-                                128..4096 from the total keys, so that the
+                                128..1024 from the total keys, so that the
                                 chunks can occupy every warp slot)          */
     int32_t use_graph;       /* 1: capture the three phases in a CUDA graph */
 } hc_batch_config;

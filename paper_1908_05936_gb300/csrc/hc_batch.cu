@@ -212,7 +212,7 @@ int auto_tile(const hc_batch_item *items, int64_t n_items) {
         if (items[i].n > 0) total += items[i].n;
     const long long per_slot = total / ((long long)sms * 64);
     int tile = 128;
-    while (tile < 4096 && (long long)tile * 2 <= per_slot) tile *= 2;
+    while (tile < 1024 && (long long)tile * 2 <= per_slot) tile *= 2;
     return tile;
 }
 

@@ -12,6 +12,15 @@ shape with the least time for the present and the absent batch together,
 the one `apply()` installs.  The winners are
 written to a JSON cache keyed by device name and SM count
 (`tuned.json` next to this file); `apply()` installs them on a table.
+
+    python -m paper_1908_05936_gb300.tune --batch [--tables 1024]
+
+tunes the batched form instead: on the multi-table workload (1024 set<u64>
+tables with capacities log-uniform in 2^10..2^22, each given 0.5 x its
+capacity in operations, 60 / 30 / 10 insert / find / erase) it times one
+batched launch for every bucket size and launch shape (lane width, keys per
+thread, block, keys per chunk) and caches the fastest as "batch/set_u64";
+`batch_config()` returns it.
 """
 from __future__ import annotations
 
@@ -195,8 +204,85 @@ def apply(table: Table) -> bool:
     return True
 
 
+def batch_candidates(bucket_bytes: int) -> list[dict]:
+    """Launch shapes of the batched form for set<u64> tables of one bucket
+    size: lock-step phases with one thread per key (lane 0) or 32-byte lanes,
+    1 or 2 keys per thread; streaming phases with 4 keys per thread; blocks
+    of 64 / 128 / 256 threads; chunks of 1024 or 4096 keys or the automatic
+    size (0)."""
+    lanes = (0, 32) if bucket_bytes > 32 else (0,)
+    out = [dict(lane_bytes=lb, keys_per_group=k, block=b, tile=t)
+           for lb in lanes for k in (1, 2) for b in (64, 128, 256) for t in (0, 1024, 4096)]
+    out += [dict(lane_bytes=0, keys_per_group=4, block=b, tile=t) for b in (64, 128, 256) for t in (0, 1024, 4096)]
+    return out
+
+
+def tune_batch(n_tables: int = 1024, buckets=(32, 64, 128), reps: int = 3, seed: int = 0, save: bool = True,
+               every: list | None = None) -> dict:
+    """Time one batched launch of the multi-table workload for every bucket
+    size and launch shape; every launch starts from cleared tables.  Returns
+    (and caches) the fastest: bucket_bytes, the shape, ms and G ops/s."""
+    from workloads import recipes
+
+    from .batch import Batch, Item
+    from .table import to_device
+    slots = recipes.multi_table_slots(n_tables, seed=seed)
+    ops = [recipes.multi_table_ops(int(sl), t, seed) for t, sl in enumerate(slots)]
+    n_ops = sum(len(o.insert_keys) + len(o.find_keys) + len(o.erase_keys) for o in ops)
+    dev = [(to_device(o.insert_keys), to_device(o.find_keys), to_device(o.erase_keys)) for o in ops]
+    outs = [tuple(torch.empty(k.numel(), dtype=torch.uint8, device="cuda") for k in d) for d in dev]
+    rows = []
+    for bb in buckets:
+        tabs = [Table(L.SET_U64, int(sl), bucket_bytes=bb) for sl in slots]
+        items = []
+        for t, (ki, kf, ke), (si, sf, se) in zip(tabs, dev, outs):
+            items += [Item(t, L.OP_INSERT, ki, None, si), Item(t, L.OP_FIND, kf, None, sf),
+                      Item(t, L.OP_ERASE, ke, None, se)]
+        for c in batch_candidates(bb):
+            batch = Batch(items, use_graph=True, **c)
+            times = []
+            for _ in range(reps + 1):
+                for t in tabs:
+                    t.clear()
+                times.append(_time_once(batch.launch))
+            batch.close()
+            ms = sorted(times[1:])[len(times[1:]) // 2]          # median of the timed launches
+            row = dict(c, bucket_bytes=bb, ms=round(ms, 4), mops=round(n_ops / ms / 1e3, 1))
+            rows.append(row)
+            if every is not None:
+                every.append(row)
+        for t in tabs:
+            t.close()
+        del items
+        torch.cuda.empty_cache()
+    best = dict(min(rows, key=lambda r: r["ms"]), tables=n_tables, ops=n_ops)
+    if save:
+        cache = {}
+        if os.path.exists(CACHE):
+            with open(CACHE) as f:
+                cache = json.load(f)
+        cache.setdefault(device_key(), {})["batch/set_u64"] = best
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return best
+
+
+def batch_config() -> dict | None:
+    """The tuned batched-form shape for set<u64> tables on the current GPU
+    (bucket_bytes, lane_bytes, keys_per_group, block, tile), or None."""
+    if not os.path.exists(CACHE):
+        return None
+    with open(CACHE) as f:
+        best = json.load(f).get(device_key(), {}).get("batch/set_u64")
+    if not best:
+        return None
+    return {k: best[k] for k in ("bucket_bytes", "lane_bytes", "keys_per_group", "block", "tile")}
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--batch", action="store_true", help="tune the batched form on the multi-table workload")
+    ap.add_argument("--tables", type=int, default=1024)
     ap.add_argument("--kinds", default="map_u64_u64,set_u64,set_u32,map_i64_i32")
     ap.add_argument("--buckets", default="32,64,128")
     ap.add_argument("--slots-log2", type=int, default=26)
@@ -205,8 +291,14 @@ def main():
     a = ap.parse_args()
     from . import build
     build.build()
-    kinds = [KIND_NAMES[k] for k in a.kinds.split(",")]
     every = [] if a.all else None
+    if a.batch:
+        best = tune_batch(a.tables, tuple(int(b) for b in a.buckets.split(",")), save=not a.no_save, every=every)
+        for row in every or []:
+            print(json.dumps(row))
+        print(json.dumps(best))
+        return
+    kinds = [KIND_NAMES[k] for k in a.kinds.split(",")]
     best = tune(kinds, tuple(int(b) for b in a.buckets.split(",")), a.slots_log2, save=not a.no_save, every=every)
     for row in every or []:
         print(json.dumps(row))
