@@ -540,6 +540,15 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def bytes_fraction(total_bytes: float, ms: float, per_op: dict, note: str) -> dict:
+    """Algorithmic bytes of a whole step (per-op minimum bytes x ops) over
+    its measured time, against the measured copy peak."""
+    peak, src = hbm_peak()
+    gbs = total_bytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "peak_source": src, "unit": "GB/s",
+            "frac": round(gbs / peak, 4), "bytes_per_op": per_op, "traffic": None, "note": note}
+
+
 # ---------------------------------------------------------- oracle (CPU) --
 
 def run_oracle_sample(args, sample_log2: int):
@@ -663,6 +672,9 @@ def run_multi_table(args):
         del items
         torch.cuda.empty_cache()
     assert arms["plain"]["live_after"] == arms["batched"]["live_after"], "plain and batched forms disagree"
+    per_op = {"insert": 8 + 1 + 32 + 32, "find": 8 + 1 + 32, "erase": 8 + 1 + 32 + 32}
+    step_bytes = sum(len(o.insert_keys) * per_op["insert"] + len(o.find_keys) * per_op["find"] +
+                     len(o.erase_keys) * per_op["erase"] for o in ops)
     return {"metric": "multi-table batched vs plain: ms per step and Mops/s", "value": arms["batched"]["mops"],
             "unit": "Mops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": arms["batched"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -672,6 +684,8 @@ def run_multi_table(args):
                        "bucket_bytes": bb, "batch_shape": dict(shape, source=source)},
             "plain": arms["plain"], "batched": arms["batched"],
             "speedup": round(arms["plain"]["ms_per_step"] / arms["batched"]["ms_per_step"], 3),
+            "roofline": bytes_fraction(step_bytes, arms["batched"]["ms_per_step"], per_op,
+                                       "whole batched launch (three phase kernels); many tables are L2-resident"),
             "gpu_launches": arms["batched"]["launches_per_step"] * args.steps}
 
 
@@ -718,6 +732,7 @@ def run_set_u32(args):
                 per[k].append(ev[j].elapsed_time(ev[j + 1]))
             per["step"].append(ev[0].elapsed_time(ev[4]))
     n = {"insert": ki.numel(), "find": kf.numel(), "erase": ke.numel()}
+    per_op = {"insert": 4 + 1 + 32 + 32, "find": 4 + 1 + 32, "erase": 4 + 1 + 32 + 32}
     med = {k: statistics.median(v) for k, v in per.items()}
     ops = sum(n.values())
     size = t.size()
@@ -729,6 +744,8 @@ def run_set_u32(args):
             "config": {"workload": "set<u32> 2^21 slots: insert 1,000,000, find 1,000,000 (50% present), erase 500,000",
                        "l2": "256 MiB flush before each step"},
             "ops": {k: {"ms": round(med[k], 4), "mops": round(n[k] / med[k] / 1e3, 1)} for k in n},
+            "roofline": bytes_fraction(sum(n[k] * per_op[k] for k in n), med["step"], per_op,
+                                       "the 8 MiB table is L2-resident: L2, not HBM, bounds it"),
             "clear_ms": round(med["clear"], 4), "final_size": size, "gpu_launches": 4 * args.steps}
 
 
@@ -892,6 +909,9 @@ def run_rgbd(args):
     final = tab.size()
     pres = [float(found[f].float().mean()) for f in range(params.frames)]
     tab.close()
+    # every candidate is looked up; the missing ones (the table's final size) are inserted
+    per_op = {"find": 8 + 4 + 1 + 32, "insert": 8 + 4 + 1 + 32 + 32}
+    step_bytes = params.frames * params.per_frame * per_op["find"] + final * per_op["insert"]
     return {"metric": "RGB-D stream: per-frame find-then-insert time and candidates/s",
             "value": res["graph"]["mcandidates_per_s"], "unit": "M candidates/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["graph"]["ms_per_stream"], "higher_is_better": True,
@@ -901,6 +921,8 @@ def run_rgbd(args):
                                    "candidate blocks, find then insert missing", "hash_mode": args.rgbd_hash,
                        "generation_s": round(gen_s, 1)},
             "eager": res["eager"], "graph": res["graph"], "final_blocks": final,
+            "roofline": bytes_fraction(step_bytes, res["graph"]["ms_per_stream"], per_op,
+                                       "find of every candidate, insert of the missing ones (graph)"),
             "final_load_factor": round(final / capacity, 4), "present_mean": round(float(np.mean(pres[1:])), 4),
             "gpu_launches": 2 * params.frames}
 

@@ -117,8 +117,10 @@ typedef struct hc_config {
  * duplicate folding in this form).  Defaults:
  * lane_bytes = the bucket's key region (one thread per key),
  * keys_per_group 4 (streaming), block 64, folding off; until hc_set_launch
- * sets an op's shape, inserts of fewer than 8192 keys per multiprocessor run
- * one key per thread in lock step.  Results never depend on the shape. */
+ * sets an op's shape, a plain insert of fewer than 8192 keys per
+ * multiprocessor and at most one key per bucket, into a table whose buckets
+ * exceed the L2 cache, runs one key per thread in lock step.  Results never
+ * depend on the shape. */
 typedef struct hc_launch {
     int32_t lane_bytes;       /* 32, 64 or 128, at most bucket_bytes     */
     int32_t keys_per_group;   /* 1 or 2; 4 or 8: streaming forms       */

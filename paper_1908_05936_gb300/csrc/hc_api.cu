@@ -67,6 +67,19 @@ int sm_count_of(int dev) {
     return cache[dev];
 }
 
+long long l2_bytes_of(int dev) {
+    static std::mutex mu;
+    static long long cache[64] = {0};
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64) return 128ll << 20;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev) != cudaSuccess || n <= 0) n = 128 << 20;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 hc_rc check_config(int kind, const hc_config *cfg, int *bb, int *hash_mode, unsigned long long *seed) {
     *bb = 32;
     *hash_mode = HC_HASH_MIX64;
@@ -187,12 +200,17 @@ hc_rc run_range(hc_table *t, int op, const void *keys, const void *vals, long lo
     if (rc != HC_OK || n == 0) return rc;
     hc::LaunchShape sh = t->shape[op];
     sh.sms = sm_count_of(t->device);
-    // Default shape, a call too small to fill the GPU with 4 keys per thread:
-    // inserts run one key per thread in lock step, which keeps more probes in
-    // flight at these sizes (measured: +5-12 % for 2^16-2^20 keys).
-    if (op == hc::OP_INSERT && !t->shape_set[op] && n < (long long)sh.sms * 8192) sh.keys_per_group = 1;
     hc::View v = t->view;
     v.rotate = n > (long long)v.nb ? 1 : 0;        // several inserters per bucket: spread them
+    // Default shape, a plain insert too small to fill the GPU with 4 keys per
+    // thread, into a table larger than L2 with at most one inserter per
+    // bucket: one key per thread in lock step, which keeps more probes in
+    // flight there (measured on a 4 GiB map: +5-12 % for 2^16-2^20 keys).
+    // Crowded or L2-resident inserts and inserts that skip keys keep the
+    // streaming form (an 8 MiB set<u32> took 2.4x as long in lock step).
+    if (op == hc::OP_INSERT && !t->shape_set[op] && !skip && !v.rotate && n < (long long)sh.sms * 8192 &&
+        (long long)v.nb * t->bucket_bytes > l2_bytes_of(t->device))
+        sh.keys_per_group = 1;
     cudaError_t e = dispatch_range(t->kind, op, v, t->bucket_bytes, keys, is_map(t->kind) ? vals : nullptr, n,
                                    out, is_map(t->kind) ? vals_out : nullptr, sh, skip, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the range kernel");
