@@ -118,3 +118,34 @@ def test_batched_maps_mixed_kinds(kpt):
     b.close()
     for t in tabs:
         t.close()
+
+
+def test_batch_tuner_sweeps_every_shape_and_its_choice_is_exact():
+    """tune.py --batch on a small multi-table workload: one timing per bucket
+    size and candidate shape, the fastest returned; the chosen shape (with
+    its bucket size) then gives the oracle's results on another workload."""
+    from paper_1908_05936_gb300 import tune
+    rows = []
+    best = tune.tune_batch(n_tables=12, buckets=(32, 64), reps=1, seed=5, save=False, every=rows)
+    assert len(rows) == len(tune.batch_candidates(32)) + len(tune.batch_candidates(64))
+    assert best["ms"] == min(r["ms"] for r in rows) and best["bucket_bytes"] in (32, 64)
+    slots, ops, _ = make_tables(24, 10, 14, seed=6)
+    tables = [Table(L.SET_U64, int(s), bucket_bytes=best["bucket_bytes"]) for s in slots]
+    items, outs = build_items(tables, ops)
+    b = Batch(items, lane_bytes=best["lane_bytes"], keys_per_group=best["keys_per_group"], block=best["block"],
+              tile=best["tile"], use_graph=True)
+    b.launch()
+    torch.cuda.synchronize()
+    for t, (o, s) in enumerate(zip(ops, slots)):
+        orc = O.OracleTable(O.SET_U64, int(s))
+        ist, (ff, _), est = orc.mixed(o.insert_keys, None, o.find_keys, o.erase_keys)
+        si, gf, se = (to_numpy(x, np.uint8) for x in outs[t])
+        C.assert_status(o.insert_keys, si, ist, f"table {t} insert")
+        C.assert_find(gf, None, ff, None, f"table {t} find")
+        C.assert_status(o.erase_keys, se, est, f"table {t} erase")
+        gk, _ = tables[t].dump_numpy()
+        ok, _ = orc.dump()
+        C.assert_contents(gk, None, ok, None, f"table {t} contents")
+    b.close()
+    for tb in tables:
+        tb.close()
