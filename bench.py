@@ -424,7 +424,8 @@ def time_ordered_mixed(t, torch, seed: int = 0) -> dict:
     of three repetitions, nothing here inside the step's timed region.
 
     * ordered insert / erase (the lowest index wins among equal keys, every
-      position gets the sequential result) of 2^24 draws from 2^23 fresh keys,
+      position gets the sequential result) of 2^24 draws from 2^23 fresh keys
+      (at most capacity / 16 draws on smaller tables),
       against the plain insert / erase of the same draws;
     * a free-running mixed batch over the same draws (50 / 30 / 20 insert /
       find / erase, per position), against the three plain calls of its parts.
@@ -432,7 +433,14 @@ def time_ordered_mixed(t, torch, seed: int = 0) -> dict:
     erased (untimed) after each timed call that inserts them."""
     from paper_1908_05936_gb300.table import to_device
     from workloads import recipes, splitmix
-    n, nd = 1 << 24, 1 << 23
+    # 2^24 draws from 2^23 keys on the 2^28-slot table; fewer on smaller
+    # tables: the mixed batch's in-kernel inserts claim EMPTY slots only, so
+    # its repetitions must leave the table most of its EMPTY slots
+    cap = t.stats()["capacity"]
+    n = 1 << 24
+    while n > 1024 and n > cap // 16:
+        n >>= 1
+    nd = n // 2
     keys_h = recipes.repeated_keys(n, nd, seed)
     ops_h = recipes.mixed_ops(n, seed=seed)
     d_keys, d_vals = to_device(keys_h), to_device(splitmix.value_of(keys_h))
