@@ -37,8 +37,10 @@ BYTES_PER_OP = {"insert": 16 + 1 + 32 + 32, "find": 8 + 8 + 1 + 32, "erase": 8 +
 # 64-byte buckets, 4 keys/thread, 2 in flight>, 64-thread blocks) on this
 # workload: dram__bytes_read.sum + dram__bytes_write.sum over the four fill
 # launches of one step at full size (one ncu capture), divided by the keys
-# they inserted.  Valid only while the kernel sources hash to `digest`.
-INSERT_TRAFFIC = {"bytes_per_op": 227.68, "digest": "2dc36df6c4a95205"}
+# they inserted; `requests_per_op` the same for lts__t_requests_srcunit_tex.sum
+# (requests from the SMs to L2).  Valid only while the kernel sources hash to
+# `digest`.
+INSERT_TRAFFIC = {"bytes_per_op": 227.68, "requests_per_op": 3.547, "digest": "2dc36df6c4a95205"}
 
 
 def insert_kernel_digest() -> str:
@@ -333,6 +335,15 @@ def run_gpu(args, rank: int, world: int):
         traffic = INSERT_TRAFFIC["bytes_per_op"] * dom_n      # DRAM bytes per launch
     peak, peak_src = hbm_peak()
     ceiling = random_read_ceiling(torch, L)
+    # the same kernel against the device's rate of scattered L2 requests
+    # (random 32-byte reads, measured above): requests per op x ops per second
+    requests = None
+    if traffic:
+        req_rate = INSERT_TRAFFIC["requests_per_op"] * dom_n / (dom_ms * 1e-3) / 1e9
+        requests = {"per_op": INSERT_TRAFFIC["requests_per_op"], "achieved": round(req_rate, 1),
+                    "ceiling": ceiling["reads_per_s"], "unit": "G L2 requests/s",
+                    "frac": round(req_rate / ceiling["reads_per_s"], 3),
+                    "source": "ncu lts__t_requests_srcunit_tex.sum, full-size capture"}
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mops/s", "n_gpus": world, "steps": args.steps,
@@ -350,7 +361,8 @@ def run_gpu(args, rank: int, world: int):
                      "traffic": round(traffic) if traffic else None, "bytes_per_op": BYTES_PER_OP[kinds[dom]],
                      "dram_gbs": round(traffic / (dom_ms * 1e-3) / 1e9, 1) if traffic else None,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, full-size capture"
-                     if traffic else "no capture for this kernel as built"},
+                     if traffic else "no capture for this kernel as built",
+                     "requests": requests},
         "random_read_ceiling": ceiling,
         "clocks": clk,
         "gpu_launches": len(calls) * world,
