@@ -66,8 +66,11 @@ def test_multi_table_full_sampled_tables():
     sample = sorted(rng.choice(len(slots), size=24, replace=False).tolist())
     ops = {t: recipes.multi_table_ops(int(slots[t]), t) for t in sample}
     tabs, items, outs = {}, [], {}
+    from paper_1908_05936_gb300 import tune
+    # the shape bench.py times: the tuner's, else the untuned default
+    shape = tune.batch_config() or dict(bucket_bytes=128, lane_bytes=0, keys_per_group=0, block=0, tile=4096)
     for t in sample:
-        tab = Table(L.SET_U64, int(slots[t]), bucket_bytes=128)
+        tab = Table(L.SET_U64, int(slots[t]), bucket_bytes=shape["bucket_bytes"])
         o = ops[t]
         ki, kf, ke = to_device(o.insert_keys), to_device(o.find_keys), to_device(o.erase_keys)
         si, ff, se = (torch.empty(x.numel(), dtype=torch.uint8, device="cuda") for x in (ki, kf, ke))
@@ -75,7 +78,8 @@ def test_multi_table_full_sampled_tables():
                   Item(tab, L.OP_ERASE, ke, None, se)]
         tabs[t] = tab
         outs[t] = (si, ff, se)
-    b = Batch(items, tile=4096, use_graph=True)
+    b = Batch(items, lane_bytes=shape["lane_bytes"], keys_per_group=shape["keys_per_group"], block=shape["block"],
+              tile=shape["tile"], use_graph=True)
     b.launch()
     torch.cuda.synchronize()
     for t in sample:
@@ -92,3 +96,50 @@ def test_multi_table_full_sampled_tables():
         orc.close()
         tabs[t].close()
     b.close()
+
+
+def test_small_inserts_into_a_table_beyond_l2():
+    """Inserts of 2^16 keys into a 256 MiB map run one key per thread in lock
+    step (the small-insert rule); with in-batch duplicates, present keys and
+    erases in between they match the oracle call by call."""
+    import gpu_pair as GP
+    rng = np.random.default_rng(2024)
+    p = GP.Pair(O.MAP_U64_U64, 1 << 24, bucket_bytes=64)
+    try:
+        dom = GP.random_keys(O.MAP_U64_U64, 1 << 18, rng)
+        for b in range(6):
+            keys = dom[rng.integers(0, len(dom), size=1 << 16)]
+            p.insert(keys, GP.value_for(O.MAP_U64_U64, keys, salt=b))
+            p.find(dom[rng.integers(0, len(dom), size=1 << 15)])
+            p.erase(keys[::5])
+        p.check()
+    finally:
+        p.close()
+
+
+def test_ordered_calls_at_scale():
+    """Ordered insert and erase of 2^20 draws from 2^19 keys (each key about
+    twice, equal keys with different values) on a 2^22-slot map, position by
+    position against the sequential oracle."""
+    rng = np.random.default_rng(2025)
+    t = Table(L.MAP_U64_U64, 1 << 22, bucket_bytes=64)
+    o = O.OracleTable(O.MAP_U64_U64, 1 << 22)
+    try:
+        dom = rng.integers(0, 2**63, size=1 << 19, dtype=np.int64).view(np.uint64)
+        keys = dom[rng.integers(0, len(dom), size=1 << 20)]
+        vals = rng.integers(0, 2**63, size=len(keys), dtype=np.int64).view(np.uint64)
+        gs = to_numpy(t.insert_ordered(to_device(keys), to_device(vals)), np.uint8)
+        assert np.array_equal(gs, o.insert(keys, vals))
+        q = dom[rng.integers(0, len(dom), size=1 << 18)]
+        gf, gv = t.find(to_device(q))
+        of, ov = o.find(q)
+        C.assert_find(to_numpy(gf, np.uint8), to_numpy(gv, np.uint64), of, ov)
+        er = dom[rng.integers(0, len(dom), size=1 << 20)]
+        ge = to_numpy(t.erase_ordered(to_device(er)), np.uint8)
+        assert np.array_equal(ge, o.erase(er))
+        gk, gvals = t.dump_numpy()
+        ok, ov = o.dump()
+        C.assert_contents(gk, gvals, ok, ov, "contents after ordered calls")
+    finally:
+        t.close()
+        o.close()
