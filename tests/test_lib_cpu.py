@@ -146,3 +146,20 @@ def test_line_read_probe_argument_errors(lib):
     assert lib.hc_measure_line_reads(ctypes.c_void_p(1 << 20), 128, 1, 1, 0, 1, ctypes.byref(ms), None) == L.ERR_ARG
     assert lib.hc_measure_line_reads(ctypes.c_void_p((1 << 20) + 64), 1 << 20, 1, 1, 0, 1, ctypes.byref(ms),
                                      None) == L.ERR_ARG
+
+
+def test_batch_tuner_candidates_and_cache(tmp_path, monkeypatch):
+    """The batched-form tuner's candidate list and cache lookup (no GPU)."""
+    import json
+    from paper_1908_05936_gb300 import tune
+    c32, c64 = tune.batch_candidates(32), tune.batch_candidates(64)
+    assert all(c["lane_bytes"] == 0 for c in c32)              # a 32-byte bucket is one 32-byte lane
+    assert len(c64) == len(c32) + 18 and {c["keys_per_group"] for c in c64} == {1, 2, 4}
+    assert all(c["block"] in (64, 128, 256) and c["tile"] in (0, 1024, 4096) for c in c64)
+    cache = tmp_path / "tuned.json"
+    monkeypatch.setattr(tune, "CACHE", str(cache))
+    monkeypatch.setattr(tune, "device_key", lambda: "dev/1SM")
+    assert tune.batch_config() is None
+    best = dict(bucket_bytes=32, lane_bytes=0, keys_per_group=1, block=128, tile=1024, ms=5.0, mops=1.0)
+    cache.write_text(json.dumps({"dev/1SM": {"batch/set_u64": best}}))
+    assert tune.batch_config() == dict(bucket_bytes=32, lane_bytes=0, keys_per_group=1, block=128, tile=1024)
