@@ -52,8 +52,10 @@ def insert_kernel_digest() -> str:
     csrc = os.path.join(ROOT, "paper_1908_05936_gb300", "csrc")
     read = lambda f: open(os.path.join(csrc, f)).read()
     stream, kernels = read("hc_stream.cuh"), read("hc_kernels.cuh")
-    parts = [read("hc_core.cuh"),
+    parts = [open(os.path.join(ROOT, "include", "hc_core.cuh")).read(),
              re.search(r"#ifndef HC_STREAM_INSERT_MINB.*?#endif", stream, re.S).group(0),
+             re.search(r"__device__ __forceinline__ void stage\(.*?\n}\n", stream, re.S).group(0),
+             re.search(r"__device__ __forceinline__ void hash_staged\(.*?\n}\n", stream, re.S).group(0),
              re.search(r"__device__ __forceinline__ void insert_stream_chunk\(.*?\n}\n", stream, re.S).group(0),
              re.search(r"template <int KIND, int BB, int KPT, int S>\n__global__[^\n]*\nk_insert_stream\(.*?\n}\n",
                        stream, re.S).group(0),

@@ -387,20 +387,6 @@ HC_API hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream);
 HC_API hc_rc hc_measure_random_reads(const void *d_buf, int64_t buf_bytes, int64_t n_reads, int32_t reps,
                                      float *ms_per_launch, void *stream);
 
-/* Device calibration: what a second request to a line costs.  One launch of
- * n_keys threads, each reading 32 bytes at the start of a pseudo-random
- * 128-byte line of d_buf (buf_bytes >= 256, 128-byte aligned, zero-filled by
- * the caller; its last 128 bytes may be overwritten); with reads_per_key 2 a
- * second 32-byte read of the same line at +32, issued together with the
- * first (dependent 0) or after it returned (dependent 1).  A map lookup
- * reads a bucket's keys, then a value in the same line: this separates the
- * cost of that second request from the line's DRAM traffic.  Mean time per
- * launch over `reps` launches after one warm-up in *ms_per_launch;
- * synchronises `stream`.  HC_ERR_ARG on bad arguments.  The paper has no
- * counterpart. */
-HC_API hc_rc hc_measure_line_reads(const void *d_buf, int64_t buf_bytes, int64_t n_keys, int32_t reads_per_key,
-                                   int32_t dependent, int32_t reps, float *ms_per_launch, void *stream);
-
 /* ---- batched form: many tables in one persistent launch -----------------
  * Not in the paper (it has one container per call); it schedules many of the
  * Section 4.1 range calls at once.  A batch holds items; each item is one

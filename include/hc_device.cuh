@@ -46,7 +46,7 @@
 #include <cuda_runtime.h>
 
 #include "hc.h"
-#include "../paper_1908_05936_gb300/csrc/hc_core.cuh"
+#include "hc_core.cuh"
 
 namespace hcd {
 

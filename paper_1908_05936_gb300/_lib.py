@@ -30,7 +30,7 @@ EXPORTS = [
     "hc_abi_version", "hc_last_error", "hc_table_bytes", "hc_create", "hc_destroy", "hc_set_launch",
     "hc_get_launch", "hc_insert", "hc_insert_if_absent", "hc_find", "hc_erase", "hc_insert_host", "hc_find_host", "hc_erase_host",
     "hc_size", "hc_stats", "hc_status", "hc_clear", "hc_rehash", "hc_dump", "hc_batch_create",
-    "hc_batch_launch", "hc_batch_destroy", "hc_batch_run_noalloc", "hc_measure_random_reads", "hc_measure_line_reads",
+    "hc_batch_launch", "hc_batch_destroy", "hc_batch_run_noalloc", "hc_measure_random_reads",
     "hc_batch_scratch_bytes", "hc_batch_run", "hc_device_view_get", "hc_select",
     "hc_ordered_scratch_bytes", "hc_insert_ordered", "hc_erase_ordered", "hc_apply_mixed",
     "hc_pack_short3", "hc_unpack_short3", "hc_server_create", "hc_server_run", "hc_server_destroy",
@@ -135,7 +135,6 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_batch_destroy": (i32, [vp]),
         "hc_batch_run_noalloc": (i32, [P(BatchItem), i64, P(BatchConfig), vp]),
         "hc_measure_random_reads": (i32, [vp, i64, i64, i32, P(ctypes.c_float), vp]),
-        "hc_measure_line_reads": (i32, [vp, i64, i64, i32, i32, i32, P(ctypes.c_float), vp]),
         "hc_batch_scratch_bytes": (i64, [i64]),
         "hc_batch_run": (i32, [P(BatchItem), i64, P(BatchConfig), vp, i64, vp]),
         "hc_device_view_get": (i32, [vp, P(DeviceView), vp]),

@@ -44,7 +44,7 @@ def _deps() -> list[str]:
 def _example_deps() -> list[str]:
     inc = os.path.join(ROOT, "include")
     return [EXAMPLES_SRC, os.path.join(inc, "hc.h"), os.path.join(inc, "hc_device.cuh"),
-            os.path.join(CSRC, "hc_core.cuh")]
+            os.path.join(inc, "hc_core.cuh")]
 
 
 def stale(lib: str = LIB) -> bool:

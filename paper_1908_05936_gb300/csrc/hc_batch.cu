@@ -147,7 +147,13 @@ size_t phase_smem(int kind, int kpt, int block) {
     if (kpt < 4) return 0;
     const int kb = kind == KIND_SET_U32 ? 4 : 8;
     const int vb = kind == KIND_SET_U32 ? 4 : 8;            // the staging holds a value slot for every kind
-    return (size_t)block * kpt * (kb + vb + 1);
+    return stream_smem((long long)block * kpt, kb, vb);
+}
+
+// A phase kernel with more than the default 48 KB of dynamic shared memory
+// must be allowed it before its occupancy is queried or it is launched.
+void allow_phase_smem(PhaseKernel k, size_t bytes) {
+    if (bytes > 48 * 1024) (void)cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int KIND, int OP>
@@ -231,7 +237,9 @@ hc_rc enqueue(hc_batch *b, cudaStream_t s) {
     for (size_t p = 0; p < b->phases.size(); ++p) {
         const hc::PhaseDesc &ph = b->phases[p];
         hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, b->lane_bytes, b->kpt);
-        k<<<b->grid[p], b->block, hc::phase_smem(ph.kind, b->kpt, b->block), s>>>(
+        const size_t smem = hc::phase_smem(ph.kind, b->kpt, b->block);
+        hc::allow_phase_smem(k, smem);
+        k<<<b->grid[p], b->block, smem, s>>>(
             b->d_items + ph.item0, ph.n_items, ph.n_chunks, b->tile, b->d_counters + ph.counter);
         e = cudaGetLastError();
         if (e != cudaSuccess) return bcuda(e, "launching a batch phase");
@@ -326,9 +334,10 @@ HC_API hc_rc hc_batch_create(hc_batch **out, const hc_batch_item *items, int64_t
     for (size_t p = 0; p < phases.size() && e == cudaSuccess; ++p) {
         int per_sm = c.blocks_per_sm;
         if (per_sm <= 0) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, hc::pick_kernel(phases[p].kind, phases[p].op, phases[p].bb, lb, kpt), block,
-                hc::phase_smem(phases[p].kind, kpt, block));
+            hc::PhaseKernel k = hc::pick_kernel(phases[p].kind, phases[p].op, phases[p].bb, lb, kpt);
+            const size_t smem = hc::phase_smem(phases[p].kind, kpt, block);
+            hc::allow_phase_smem(k, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
             if (per_sm <= 0) per_sm = 1;
         }
         long long g = (long long)sms * per_sm;
@@ -521,16 +530,18 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
     for (int p = 0; p < n_phases; ++p) {
         const hc::PhaseDesc &ph = phases[p];
         hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, lb, kpt);
+        const size_t smem = hc::phase_smem(ph.kind, kpt, block);
+        hc::allow_phase_smem(k, smem);
         int per_sm = c.blocks_per_sm;
         if (per_sm <= 0) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, hc::phase_smem(ph.kind, kpt, block));
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem);
             if (e != cudaSuccess) return bcuda(e, "querying occupancy");
             if (per_sm <= 0) per_sm = 1;
         }
         long long g = (long long)sms * per_sm;
         const long long need = kpt >= 4 ? ph.n_chunks : (ph.n_chunks * 32 + block - 1) / block;
         if (g > need) g = need;
-        k<<<(unsigned)(g > 0 ? g : 1), block, hc::phase_smem(ph.kind, kpt, block), s>>>(
+        k<<<(unsigned)(g > 0 ? g : 1), block, smem, s>>>(
             scratch->items + ph.item0, ph.n_items, ph.n_chunks, tile, scratch->counters + ph.counter);
         e = cudaGetLastError();
         if (e != cudaSuccess) return bcuda(e, "launching a batch phase");
@@ -648,6 +659,7 @@ hc_rc batch_run(const hc_batch_item *items, int64_t n_items, const hc_batch_conf
         hc::PhaseKernel k = hc::pick_kernel(ph.kind, ph.op, ph.bb, lb, kpt);
         int per_sm = c.blocks_per_sm;
         const size_t smem = hc::phase_smem(ph.kind, kpt, block);
+        hc::allow_phase_smem(k, smem);
         if (per_sm <= 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess) per_sm = 1;
         if (per_sm <= 0) per_sm = 1;
         long long g = (long long)sms * per_sm;

@@ -175,6 +175,14 @@ cudaError_t launch_range_shape(int op, const View &v, const void *keys, const vo
     return cudaGetLastError();
 }
 
+// A kernel launched with more than the default 48 KB of dynamic shared
+// memory (streaming kernels with 256-thread blocks and 8 keys per thread)
+// must be allowed it first.
+template <class K>
+void allow_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) (void)cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // Streaming lookup: each thread owns KPT keys of its block's staged chunk and
 // keeps S probes in flight (find only, one thread per key).
 template <int KIND, int BB, int KPT, int S>
@@ -183,7 +191,8 @@ cudaError_t launch_find_stream(const View &v, const void *keys, long long n, uin
     using T = Traits<KIND>;
     const long long chunk = (long long)block * KPT;
     const unsigned grid = (unsigned)((n + chunk - 1) / chunk);
-    const size_t smem = (size_t)chunk * (sizeof(typename T::Key) + sizeof(typename T::Val) + 1);
+    const size_t smem = stream_smem(chunk, sizeof(typename T::Key), sizeof(typename T::Val));
+    allow_smem(k_find_stream<KIND, BB, KPT, S>, smem);
     k_find_stream<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys, n, out,
                                                               (typename T::Val *)vals_out);
     return cudaGetLastError();
@@ -207,7 +216,8 @@ cudaError_t launch_insert_stream(const View &v, const void *keys, const void *va
     using T = Traits<KIND>;
     const long long chunk = (long long)block * KPT;
     const unsigned grid = (unsigned)((n + chunk - 1) / chunk);
-    const size_t smem = (size_t)chunk * (sizeof(typename T::Key) + sizeof(typename T::Val) + 1);
+    const size_t smem = stream_smem(chunk, sizeof(typename T::Key), sizeof(typename T::Val));
+    allow_smem(k_insert_stream<KIND, BB, KPT, S>, smem);
     k_insert_stream<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys,
                                                                 (const typename T::Val *)vals, n, out, skip);
     return cudaGetLastError();
@@ -219,7 +229,8 @@ cudaError_t launch_erase_stream(const View &v, const void *keys, long long n, ui
     using T = Traits<KIND>;
     const long long chunk = (long long)block * KPT;
     const unsigned grid = (unsigned)((n + chunk - 1) / chunk);
-    const size_t smem = (size_t)chunk * (sizeof(typename T::Key) + 1);
+    const size_t smem = stream_smem(chunk, sizeof(typename T::Key), 0);
+    allow_smem(k_erase_stream<KIND, BB, KPT, S>, smem);
     k_erase_stream<KIND, BB, KPT, S><<<grid, block, smem, s>>>(v, (const typename T::Key *)keys, n, out, skip);
     return cudaGetLastError();
 }

@@ -27,66 +27,7 @@ __global__ void __launch_bounds__(256) k_random_reads(const unsigned char *buf, 
     if (((a ^ b ^ c ^ d) & 0xFFFFFFFFFull) == 0x123456789ull) *sink = a;   // keeps the load alive
 }
 
-// One key per thread: a random 128-byte line, read 32 bytes at its start;
-// TWO: a second 32-byte read of the same line, at +32, either issued with the
-// first (DEP false) or after the first returned (DEP true: its offset depends
-// on the loaded data, and is 0 for the zero-filled buffers this is run on).
-template <bool TWO, bool DEP>
-__global__ void __launch_bounds__(256) k_line_reads(const unsigned char *buf, unsigned long long lines, long long n,
-                                                    unsigned long long salt, unsigned long long *sink) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const unsigned char *p = buf + __umul64hi(scramble((unsigned long long)i ^ salt), lines) * 128;   // line < lines
-    unsigned long long a, b, c, d, e = 0, f = 0, g = 0, h = 0;
-    asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
-    if (TWO) {
-        const unsigned long long off = (DEP && a == 0x123456789ull) ? 64 : 0;   // still inside the line
-        asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
-                     : "=l"(e), "=l"(f), "=l"(g), "=l"(h) : "l"(p + 32 + off));
-    }
-    if (((a ^ b ^ c ^ d ^ e ^ f ^ g ^ h) & 0xFFFFFFFFFull) == 0x123456789ull) *sink = a;
-}
-
 }  // namespace
-
-extern "C" HC_API hc_rc hc_measure_line_reads(const void *d_buf, int64_t buf_bytes, int64_t n_keys,
-                                              int32_t reads_per_key, int32_t dependent, int32_t reps,
-                                              float *ms_per_launch, void *stream) {
-    if (!d_buf || buf_bytes < 256 || n_keys < 1 || reps < 1 || !ms_per_launch ||
-        (reads_per_key != 1 && reads_per_key != 2) || (dependent != 0 && dependent != 1) ||
-        reinterpret_cast<uintptr_t>(d_buf) % 128)
-        return HC_ERR_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the last line of the buffer receives the sink word
-    const unsigned long long lines = (unsigned long long)(buf_bytes / 128) - 1;
-    unsigned long long *sink = reinterpret_cast<unsigned long long *>(
-        const_cast<unsigned char *>(static_cast<const unsigned char *>(d_buf)) + lines * 128);
-    const unsigned grid = (unsigned)((n_keys + 255) / 256);
-    auto run = [&](unsigned long long salt) {
-        const unsigned char *b = static_cast<const unsigned char *>(d_buf);
-        if (reads_per_key == 1) k_line_reads<false, false><<<grid, 256, 0, s>>>(b, lines, n_keys, salt, sink);
-        else if (!dependent) k_line_reads<true, false><<<grid, 256, 0, s>>>(b, lines, n_keys, salt, sink);
-        else k_line_reads<true, true><<<grid, 256, 0, s>>>(b, lines, n_keys, salt, sink);
-    };
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return HC_ERR_CUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return HC_ERR_CUDA;
-    }
-    run(1);
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < reps; ++r) run(2 + (unsigned long long)r);
-    cudaEventRecord(e1, s);
-    cudaError_t e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (e != cudaSuccess) return HC_ERR_CUDA;
-    *ms_per_launch = ms / reps;
-    return HC_OK;
-}
 
 extern "C" HC_API hc_rc hc_measure_random_reads(const void *d_buf, int64_t buf_bytes, int64_t n_reads, int32_t reps,
                                                 float *ms_per_launch, void *stream) {

@@ -1,9 +1,11 @@
-// hc_stream.cuh -- streaming lookup: a block stages its chunk of query keys in
-// shared memory with coalesced loads, then every thread keeps S probes in
-// flight and refills a slot from the chunk as soon as its probe finishes
-// (instead of moving its keys in lock-step rounds).  Found flags and values
-// go to shared memory and leave in coalesced stores.  One thread per key,
-// reading the bucket's key region (KRB bytes) per probe.
+// hc_stream.cuh -- the streaming range kernels: a block stages its chunk of
+// keys (and values) in shared memory with coalesced 16-byte loads and
+// computes every staged key's first bucket there, so neither the key load nor
+// the hash sits on a key's chain of dependent reads.  Every thread then keeps
+// S probes in flight and refills a slot from the chunk as soon as its probe
+// finishes (instead of moving its keys in lock-step rounds).  Results go to
+// shared memory and leave in coalesced stores.  One thread per key, reading
+// the bucket's key region (KRB bytes) per probe.
 #pragma once
 
 #include "hc_core.cuh"
@@ -30,6 +32,42 @@
 #endif
 
 namespace hc {
+
+// Copies m elements from src (global) to dst (shared, 16-byte aligned) with
+// the whole block: 16 bytes per load where src is 16-byte aligned, element by
+// element otherwise and for the tail.
+template <class T>
+__device__ __forceinline__ void stage(T *dst, const T *src, int m) {
+    constexpr int E = 16 / (int)sizeof(T);
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int nv = m / E;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) d4[i] = __ldcs(s4 + i);
+        done = nv * E;
+    }
+    for (int i = done + (int)threadIdx.x; i < m; i += blockDim.x) dst[i] = ld_stream(src + i);
+}
+
+// Dynamic shared memory of the streaming kernels for a chunk of `chunk`
+// keys: per key its first bucket, key, value (vb bytes; 0 for erase) and
+// result byte.
+__host__ __device__ __forceinline__ size_t stream_smem(long long chunk, int kb, int vb) {
+    return (size_t)chunk * (8 + kb + vb + 1);
+}
+
+// First buckets of the keys thread t will take (t, t + nt, ...), computed
+// right after staging, while every thread of the block does the same work.
+template <int KIND, int KPT>
+__device__ __forceinline__ void hash_staged(const View &v, const typename Traits<KIND>::Key *sk,
+                                            unsigned long long *sb, int m) {
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        const int i = threadIdx.x + j * blockDim.x;
+        if (i < m) sb[i] = first_bucket(v, (unsigned long long)sk[i]);
+    }
+}
 
 template <int LB>
 __device__ __forceinline__ void load_find(LaneWords<LB> &lw, const unsigned char *p) {
@@ -65,13 +103,15 @@ __device__ __forceinline__ void find_stream_chunk(const View &v, const typename 
     extern __shared__ __align__(16) unsigned char smem[];
     const int nt = blockDim.x;
     const int chunk = nt * KPT;
-    Key *sk = reinterpret_cast<Key *>(smem);
-    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * sizeof(Key));
-    uint8_t *sf = smem + (size_t)chunk * (sizeof(Key) + sizeof(Val));
+    unsigned long long *sb = reinterpret_cast<unsigned long long *>(smem);
+    Key *sk = reinterpret_cast<Key *>(smem + (size_t)chunk * 8);
+    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * (8 + sizeof(Key)));
+    uint8_t *sf = smem + (size_t)chunk * (8 + sizeof(Key) + sizeof(Val));
 
     __syncthreads();                         // the staging of a previous chunk is no longer read
-    for (int i = threadIdx.x; i < m; i += nt) sk[i] = ld_stream(keys + c0 + i);
+    stage(sk, keys + c0, m);
     __syncthreads();
+    hash_staged<KIND, KPT>(v, sk, sb, m);
 
     // this thread's keys: threadIdx.x + j * nt, j < KPT
     int idx[S];
@@ -94,7 +134,7 @@ __device__ __forceinline__ void find_stream_chunk(const View &v, const typename 
             }
             idx[s] = i;
             key[s] = k;
-            b[s] = first_bucket(v, (unsigned long long)k);
+            b[s] = sb[i];
             probes[s] = 0;
             active |= 1u << s;
             return;
@@ -182,7 +222,7 @@ k_find_pair(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t
 
     const long long c0 = (long long)blockIdx.x * chunk;
     const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) sk[i] = ld_stream(keys + c0 + i);
+    stage(sk, keys + c0, m);
     __syncthreads();
 
     const unsigned lane = threadIdx.x & 31;
@@ -321,17 +361,18 @@ __device__ __forceinline__ void insert_stream_chunk(const View &v, const typenam
     extern __shared__ __align__(16) unsigned char smem[];
     const int nt = blockDim.x;
     const int chunk = nt * KPT;
-    Key *sk = reinterpret_cast<Key *>(smem);
-    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * sizeof(Key));
-    uint8_t *ss = smem + (size_t)chunk * (sizeof(Key) + sizeof(Val));
+    unsigned long long *sb = reinterpret_cast<unsigned long long *>(smem);
+    Key *sk = reinterpret_cast<Key *>(smem + (size_t)chunk * 8);
+    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * (8 + sizeof(Key)));
+    uint8_t *ss = smem + (size_t)chunk * (8 + sizeof(Key) + sizeof(Val));
 
     __syncthreads();                         // the staging of a previous chunk is no longer read
-    for (int i = threadIdx.x; i < m; i += nt) {
-        sk[i] = ld_stream(keys + c0 + i);
-        if constexpr (T::MAP) sv[i] = ld_stream(vals + c0 + i);
+    stage(sk, keys + c0, m);
+    if constexpr (T::MAP) stage(sv, vals + c0, m);
+    for (int i = threadIdx.x; i < m; i += nt)
         ss[i] = (skip && ld_stream(skip + c0 + i)) ? (uint8_t)ST_EXISTS : (uint8_t)0xFF;   // 0xFF: to do
-    }
     __syncthreads();
+    hash_staged<KIND, KPT>(v, sk, sb, m);
 
     Counts cnt;
     int idx[S];
@@ -359,7 +400,7 @@ __device__ __forceinline__ void insert_stream_chunk(const View &v, const typenam
             }
             idx[s] = i;
             key[s] = k;
-            b[s] = first_bucket(v, (unsigned long long)k);
+            b[s] = sb[i];
             probes[s] = 0;
             restarts[s] = 0;
             ffb[s] = ~0ull;
@@ -489,15 +530,16 @@ __device__ __forceinline__ void erase_stream_chunk(const View &v, const typename
     extern __shared__ __align__(16) unsigned char smem[];
     const int nt = blockDim.x;
     const int chunk = nt * KPT;
-    Key *sk = reinterpret_cast<Key *>(smem);
-    uint8_t *ss = smem + (size_t)chunk * sizeof(Key);
+    unsigned long long *sb = reinterpret_cast<unsigned long long *>(smem);
+    Key *sk = reinterpret_cast<Key *>(smem + (size_t)chunk * 8);
+    uint8_t *ss = smem + (size_t)chunk * (8 + sizeof(Key));
 
     __syncthreads();                         // the staging of a previous chunk is no longer read
-    for (int i = threadIdx.x; i < m; i += nt) {
-        sk[i] = ld_stream(keys + c0 + i);
+    stage(sk, keys + c0, m);
+    for (int i = threadIdx.x; i < m; i += nt)
         ss[i] = (skip && ld_stream(skip + c0 + i)) ? (uint8_t)ST_NOT_FOUND : (uint8_t)0xFF;   // 0xFF: to do
-    }
     __syncthreads();
+    hash_staged<KIND, KPT>(v, sk, sb, m);
 
     Counts cnt;
     int idx[S];
@@ -521,7 +563,7 @@ __device__ __forceinline__ void erase_stream_chunk(const View &v, const typename
             }
             idx[s] = i;
             key[s] = k;
-            b[s] = first_bucket(v, (unsigned long long)k);
+            b[s] = sb[i];
             probes[s] = 0;
             active |= 1u << s;
             return;

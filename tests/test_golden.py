@@ -12,7 +12,7 @@ def test_teschner_constants_match_the_paper():
         if line.strip() and not line.startswith("#"):
             axis, c = line.split()
             golden[axis] = int(c)
-    src = open(os.path.join(ROOT, "paper_1908_05936_gb300", "csrc", "hc_core.cuh")).read()
+    src = open(os.path.join(ROOT, "include", "hc_core.cuh")).read()
     body = src[src.index("teschner(unsigned long long key)"):]
     body = body[:body.index("\n}\n")]
     used = dict(re.findall(r"\((\w) \* (\d+)ull\)", body))

@@ -430,16 +430,3 @@ def test_binding_refuses_short_buffers():
         assert to_numpy(f, np.uint8).all() and np.array_equal(to_numpy(vo, np.uint64), np.arange(1, 101))
     finally:
         t.close()
-
-
-def test_line_read_calibration_runs():
-    """hc_measure_line_reads in its three modes on a small zeroed buffer."""
-    import ctypes
-    from paper_1908_05936_gb300 import _lib as L
-    buf = torch.zeros(1 << 24, dtype=torch.uint8, device="cuda")
-    for reads, dep in ((1, 0), (2, 0), (2, 1)):
-        ms = ctypes.c_float()
-        L.check(L.load().hc_measure_line_reads(buf.data_ptr(), buf.numel(), 1 << 16, reads, dep, 2, ctypes.byref(ms),
-                                               torch.cuda.current_stream().cuda_stream))
-        assert ms.value > 0
-    assert int(buf[:-128].sum().item()) == 0          # reads only, outside the sink line

@@ -136,16 +136,15 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert got == want
 
 
-def test_line_read_probe_argument_errors(lib):
-    """hc_measure_line_reads refuses bad arguments before any launch."""
+def test_random_read_probe_argument_errors(lib):
+    """hc_measure_random_reads refuses bad arguments before any launch."""
     from paper_1908_05936_gb300 import _lib as L
     ms = ctypes.c_float()
-    assert lib.hc_measure_line_reads(None, 1 << 20, 1, 1, 0, 1, ctypes.byref(ms), None) == L.ERR_ARG
-    assert lib.hc_measure_line_reads(ctypes.c_void_p(1 << 20), 1 << 20, 1, 3, 0, 1, ctypes.byref(ms), None) == L.ERR_ARG
-    assert lib.hc_measure_line_reads(ctypes.c_void_p(1 << 20), 1 << 20, 1, 2, 2, 1, ctypes.byref(ms), None) == L.ERR_ARG
-    assert lib.hc_measure_line_reads(ctypes.c_void_p(1 << 20), 128, 1, 1, 0, 1, ctypes.byref(ms), None) == L.ERR_ARG
-    assert lib.hc_measure_line_reads(ctypes.c_void_p((1 << 20) + 64), 1 << 20, 1, 1, 0, 1, ctypes.byref(ms),
-                                     None) == L.ERR_ARG
+    assert lib.hc_measure_random_reads(None, 1 << 20, 1, 1, ctypes.byref(ms), None) == L.ERR_ARG
+    assert lib.hc_measure_random_reads(ctypes.c_void_p(1 << 20), 32, 1, 1, ctypes.byref(ms), None) == L.ERR_ARG
+    assert lib.hc_measure_random_reads(ctypes.c_void_p(1 << 20), 1 << 20, 0, 1, ctypes.byref(ms), None) == L.ERR_ARG
+    assert lib.hc_measure_random_reads(ctypes.c_void_p((1 << 20) + 16), 1 << 20, 1, 1, ctypes.byref(ms),
+                                       None) == L.ERR_ARG
 
 
 def test_batch_tuner_candidates_and_cache(tmp_path, monkeypatch):
