@@ -33,6 +33,8 @@ def assert_status(keys, got, exp, what="status"):
     got = np.asarray(got)
     exp = np.asarray(exp)
     assert got.shape == exp.shape, what
+    if np.array_equal(got, exp):          # equal at every position: the multisets are equal too
+        return
     if not status_multiset_equal(keys, got, exp):
         bad = np.nonzero(got != exp)[0][:10]
         raise AssertionError(f"{what}: (key, status) multisets differ; first differing positions {bad}, "

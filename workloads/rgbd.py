@@ -129,6 +129,15 @@ def frame_keys(p: RGBDParams, f: int) -> np.ndarray:
     return pack(b[:, 0], b[:, 1], b[:, 2])
 
 
+def all_frame_keys(p: RGBDParams, workers: int = 8) -> list[np.ndarray]:
+    """frame_keys for every frame, computed by a process pool started with
+    spawn (safe in a process that already holds a CUDA context)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(frame_keys, [p] * p.frames, range(p.frames), chunksize=4))
+
+
 def values_of(keys: np.ndarray) -> np.ndarray:
     """Mapped value: hash(key) mod 2^31 as int32 (splitmix64 of the key)."""
     return (sm.value_of(np.asarray(keys, dtype=np.int64).view(np.uint64)) % np.uint64(1 << 31)).astype(np.int32)
