@@ -80,6 +80,8 @@ def parse():
                     help="lane bytes of the lookups only (the bucket size: lane-pair lookups for maps)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the batched, served, RGB-D and set<u32> comparisons")
     ap.add_argument("--cpu-sample-log2", type=int, default=24)
     ap.add_argument("--workload", default="map_sweep",
                     choices=["map_sweep", "map_grid", "device_api", "multi_table", "served", "rgbd", "set_u32"])
@@ -365,6 +367,13 @@ def run_gpu(args, rank: int, world: int):
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, full-size capture"
                      if traffic else "no capture for this kernel as built",
                      "requests": requests},
+        "at_lf08": {"insert_mops": summary["insert_by_batch"][-1]["mops"],
+                    "insert_batch_lf": [round(max(0.0, (nb - 1) * B / wl.slots), 3), summary["insert_by_batch"][-1]["lf_end"]],
+                    "find_hit_mops": round(summary["find_hit"]["mops"], 1),
+                    "find_miss_mops": round(summary["find_miss"]["mops"], 1),
+                    "erase_mops": round(summary["erase"]["mops"], 1),
+                    "note": "insert: the fill's last batch (load factor from..to); lookups and erase run on the "
+                            "table at load factor 0.8"},
         "random_read_ceiling": ceiling,
         "clocks": clk,
         "gpu_launches": len(calls) * world,
@@ -1047,6 +1056,63 @@ def run_served(args):
             "loads": loads, "clocks": clk}
 
 
+def run_extras(args) -> dict:
+    """The other configurations, each after the timed region of the headline
+    step and outside it: the batched form against per-table launches, the
+    served form against one launch per request, the RGB-D stream, and the
+    L2-resident set<u32> workload.  Compact summaries; a workload that fails
+    reports its error instead of ending the run."""
+    import copy
+    import torch
+    res = {}
+    for name, fn, pick in (("multi_table", run_multi_table, _pick_multi), ("served", run_served, _pick_served),
+                           ("rgbd", run_rgbd, _pick_rgbd), ("set_u32", run_set_u32, _pick_set_u32)):
+        a = copy.copy(args)
+        a.workload = name
+        t0 = time.perf_counter()
+        try:
+            res[name] = pick(fn(a))
+        except Exception as e:                     # reported, not fatal: the headline line stands
+            res[name] = {"error": f"{type(e).__name__}: {e}"}
+        res[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
+    return res
+
+
+def _pick_multi(r):
+    return {"config": r["config"]["workload"], "shape": r["config"]["batch_shape"],
+            "plain_ms": r["plain"]["ms_per_step"], "batched_ms": r["batched"]["ms_per_step"],
+            "speedup": r["speedup"], "batched_mops": r["batched"]["mops"], "plain_mops": r["plain"]["mops"],
+            "launches": {"plain": r["plain"]["launches_per_step"], "batched": r["batched"]["launches_per_step"]},
+            "same_size": r["plain"]["live_after"] == r["batched"]["live_after"],
+            "roofline_frac": r["roofline"]["frac"]}
+
+
+def _pick_served(r):
+    cap = r["capacity"]
+    return {"config": r["config"]["workload"],
+            "capacity_mops": {"plain": cap["plain"]["mops"], "merged": cap["merged"]["mops"]},
+            "capacity_launches": {"plain": cap["plain"]["launches"], "merged": cap["merged"]["launches"]},
+            "latency_ms": {load: {form: {"p50": v[form]["p50_ms"], "p99": v[form]["p99_ms"], "mops": v[form]["mops"]}
+                                  for form in ("plain", "merged")} | {"rate_req_per_s": v["rate_req_per_s"]}
+                           for load, v in r["loads"].items()},
+            "clocks": r["clocks"]}
+
+
+def _pick_rgbd(r):
+    return {"config": r["config"]["workload"], "ms_per_frame": {"eager": r["eager"]["ms_per_frame"],
+                                                                "graph": r["graph"]["ms_per_frame"]},
+            "mcandidates_per_s": r["graph"]["mcandidates_per_s"], "final_blocks": r["final_blocks"],
+            "final_load_factor": r["final_load_factor"], "present_mean": r["present_mean"],
+            "roofline_frac": r["roofline"]["frac"]}
+
+
+def _pick_set_u32(r):
+    return {"config": r["config"]["workload"], "mops": {k: v["mops"] for k, v in r["ops"].items()},
+            "ms": {k: v["ms"] for k, v in r["ops"].items()}, "final_size": r["final_size"],
+            "note": r["roofline"]["note"]}
+
+
 def main():
     args = parse()
     if args.workload == "multi_table":
@@ -1078,10 +1144,14 @@ def main():
         v = statistics.median(x["value"] for x in vals)
         cb = dict(vals[-1])
         cb["value"] = v
+        n_s = 1 << args.cpu_sample_log2
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mops/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded splitmix64 keys)",
-                "config": {"workload": wl.name, "slots": wl.slots, "batch": wl.batch, "load_factor": args.lf},
+                "config": {"workload": f"map<u64,u64> {wl.slots} slots (capacity), timed on a bounded sample: "
+                                       f"fill {n_s} keys, find {n_s // 4} hit + {n_s // 4} miss, erase {n_s // 4} "
+                                       f"(the GPU arm's workload: {wl.name})",
+                           "slots": wl.slots, "sample_keys": n_s, "batch": wl.batch, "load_factor": args.lf},
                 "cpu_baseline": cb, "e2e": {"value": v, "unit": "Mops/s", "h2d_bytes_per_step": 0,
                                             "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -1093,6 +1163,9 @@ def main():
     if rank == 0:
         if not args.no_cpu and args.workload == "map_sweep":
             out["cpu_baseline"] = run_oracle_sample(args, args.cpu_sample_log2)
+        shaped = args.bucket_bytes or args.lane_bytes or args.kpt or args.block or args.find_lane_bytes
+        if world == 1 and args.workload == "map_sweep" and not args.no_extras and not shaped:
+            out["workloads"] = run_extras(args)
         print(json.dumps(out))
     if world > 1:
         import torch

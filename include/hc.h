@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define HC_ABI_VERSION 1
+#define HC_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define HC_API __attribute__((visibility("default")))
@@ -69,7 +69,10 @@ typedef enum hc_rc {
     HC_ERR_OOM = 2,       /* device allocation failed                    */
     HC_ERR_OVERFLOW = 3,  /* an insert found the table full (sticky)     */
     HC_ERR_CUDA = 4,      /* a CUDA runtime call failed                  */
-    HC_ERR_STATE = 5      /* a device-side bound was hit (see hc_stats)  */
+    HC_ERR_STATE = 5,     /* a device-side bound was hit (see hc_stats), or
+                             a served run or wait could not complete       */
+    HC_ERR_TIMEOUT = 6    /* a served request's deadline passed before it
+                             was dispatched; nothing of it ran            */
 } hc_rc;
 
 /* Per-key status bytes written by insert and erase. */
@@ -471,7 +474,7 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
  * Not in the paper (which has one container per call); it serves the range
  * calls of Section 4.1 to a stream of requests over resident tables.  A
  * request is one insert / find / erase of a host key array on one table.
- * The loop, run on the calling host thread:
+ * The loop:
  *   1. an arrived request joins its table's FIFO; a table belongs to one lane
  *      (a CUDA stream, table index mod lanes), so its requests reach the GPU
  *      in arrival order;
@@ -482,17 +485,29 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
  *   3. a free slot takes the heads of its lane's FIFOs, one per table, while
  *      they fit (at most max_items), copies their inputs host->device (small
  *      requests packed into one copy), runs one hc_batch_run over them
- *      (merge = 1) or one range call each (merge = 0), copies the results
+ *      (merge = 1; a slot holding a single request runs its range call
+ *      instead) or one range call each (merge = 0), copies the results
  *      device->host and records an event;
  *   4. a finished slot hands each request its results and completion time.
- * Requests wait for a slot; none is dropped.  A request bigger than a slot is
- * HC_ERR_ARG before anything runs. */
+ * A request larger than a slot is cut into chunks that fit, run one after
+ * another before the table's next request; each chunk is one concurrent
+ * batch of the request's operation.  Requests wait for a slot; a request is
+ * dropped only when its deadline passes before any of it was dispatched.
+ *
+ * Two ways to feed the loop:
+ *   - hc_server_run: a list of requests with arrival times, served on the
+ *     calling thread; returns when every request is done;
+ *   - hc_server_start: the loop runs on a thread of the server's own;
+ *     hc_server_submit hands it requests from any host thread while it runs
+ *     (they arrive when submitted), hc_server_wait blocks until one is done,
+ *     hc_server_stop serves what was submitted and ends the loop.
+ * One server runs one loop at a time. */
 typedef struct hc_server hc_server;
 
 typedef struct hc_serve_config {
     int32_t lanes;           /* streams (default 4)                              */
     int32_t depth;           /* launch slots per lane (default 2)                */
-    int64_t slot_bytes;      /* device (and pinned host) bytes per slot (default 64 MiB) */
+    int64_t slot_bytes;      /* device (and pinned host) bytes per slot (default 64 MiB, at least 64 KiB) */
     int32_t merge;           /* 1: one batched launch per slot; 0: one call per request */
     int32_t max_items;       /* requests per merged launch (default 256, at most 4096) */
     hc_batch_config batch;   /* shape of the merged launches (use_graph must be 0) */
@@ -506,16 +521,23 @@ typedef struct hc_request {
     int64_t n;               /* keys                                            */
     uint8_t *h_status;       /* host output: insert/erase status or found flags  */
     void *h_vals_out;        /* host output: values of a map find, may be NULL   */
-    double arrival;          /* seconds after the run starts                     */
+    double arrival;          /* seconds after the loop started: given to
+                                hc_server_run; written by hc_server_submit       */
+    double deadline;         /* seconds after arrival by which the request must
+                                be dispatched, else it is dropped (0: none)      */
     double done;             /* written: seconds after the start when the host
-                                holds the results                                */
+                                holds the results (or the request was dropped)  */
+    int32_t rc;              /* written: HC_OK when served, HC_ERR_TIMEOUT when
+                                dropped; -1 while queued or running              */
+    int32_t reserved;
 } hc_request;
 
 typedef struct hc_serve_stats {
     int64_t requests, ops, launches, queued_max;
+    int64_t timed_out;                        /* requests dropped at their deadline */
     double wall_s;
-    double p50_ms, p99_ms, p999_ms, max_ms;   /* latency: arrival (0 when not
-                                                 realtime) to done            */
+    double p50_ms, p99_ms, p999_ms, max_ms;   /* latency of the served requests:
+                                                 arrival (0 when not realtime) to done */
 } hc_serve_stats;
 
 /* tables: n_tables handles on the current device; the server keeps the
@@ -524,11 +546,30 @@ HC_API hc_rc hc_server_create(hc_server **out, hc_table *const *tables, int32_t 
 /* Serve `reqs` (sorted by arrival).  realtime = 1 admits a request when its
  * arrival time has passed; 0 treats every request as arrived at the start (a
  * capacity run).  Synchronises the device first (work queued on any stream
- * before the run comes first).  Returns when every request is done
- * (HC_ERR_STATE after timeout_s seconds).  Fills each request's outputs and
- * `done`, and *stats (may be NULL). */
+ * before the run comes first).  Returns when every request is done or
+ * dropped (HC_ERR_STATE after timeout_s seconds).  Fills each request's
+ * outputs, `done` and `rc`, and *stats (may be NULL).  HC_ERR_ARG while the
+ * server's own loop is running. */
 HC_API hc_rc hc_server_run(hc_server *srv, hc_request *reqs, int64_t n_reqs, int32_t realtime, double timeout_s,
                            hc_serve_stats *stats);
+/* Start the server's own loop on a new host thread (synchronises the device
+ * first).  The loop uses the tables' device and the server's streams. */
+HC_API hc_rc hc_server_start(hc_server *srv);
+/* Hand *req to the running loop; callable from any host thread, returns at
+ * once.  req->arrival is set to now; the request and its arrays must stay
+ * valid, and must not be read or written by the caller, until
+ * hc_server_wait on it returned (or hc_server_stop did).  HC_ERR_STATE if
+ * the loop is not running or is stopping. */
+HC_API hc_rc hc_server_submit(hc_server *srv, hc_request *req);
+/* Block until *req (submitted to this server) is done: HC_OK with its
+ * outputs filled, HC_ERR_TIMEOUT if its deadline passed before it was
+ * dispatched, or HC_ERR_TIMEOUT / HC_ERR_STATE if timeout_s passed or the
+ * loop ended first. */
+HC_API hc_rc hc_server_wait(hc_server *srv, hc_request *req, double timeout_s);
+/* Serve every submitted request, end the loop and join its thread; *stats
+ * (may be NULL) receives the loop's statistics. */
+HC_API hc_rc hc_server_stop(hc_server *srv, hc_serve_stats *stats);
+/* Destroy a server (stops its loop first if it runs). */
 HC_API hc_rc hc_server_destroy(hc_server *srv);
 
 #ifdef __cplusplus

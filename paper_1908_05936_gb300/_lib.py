@@ -16,8 +16,9 @@ LIB_PATH = os.path.join(HERE, "libhc.so")
 # hc_kind
 SET_U32, SET_U64, MAP_I64_I32, MAP_U64_U64 = 0, 1, 2, 3
 # hc_rc
-OK, ERR_ARG, ERR_OOM, ERR_OVERFLOW, ERR_CUDA, ERR_STATE = 0, 1, 2, 3, 4, 5
-RC_NAMES = {0: "HC_OK", 1: "HC_ERR_ARG", 2: "HC_ERR_OOM", 3: "HC_ERR_OVERFLOW", 4: "HC_ERR_CUDA", 5: "HC_ERR_STATE"}
+OK, ERR_ARG, ERR_OOM, ERR_OVERFLOW, ERR_CUDA, ERR_STATE, ERR_TIMEOUT = 0, 1, 2, 3, 4, 5, 6
+RC_NAMES = {0: "HC_OK", 1: "HC_ERR_ARG", 2: "HC_ERR_OOM", 3: "HC_ERR_OVERFLOW", 4: "HC_ERR_CUDA", 5: "HC_ERR_STATE",
+            6: "HC_ERR_TIMEOUT"}
 # per-key status
 INSERTED, EXISTS, OVERFLOW, ERASED, NOT_FOUND = 0, 1, 2, 3, 4
 # selection predicates
@@ -34,6 +35,7 @@ EXPORTS = [
     "hc_batch_scratch_bytes", "hc_batch_run", "hc_device_view_get", "hc_select",
     "hc_ordered_scratch_bytes", "hc_insert_ordered", "hc_erase_ordered", "hc_apply_mixed",
     "hc_pack_short3", "hc_unpack_short3", "hc_server_create", "hc_server_run", "hc_server_destroy",
+    "hc_server_start", "hc_server_submit", "hc_server_wait", "hc_server_stop",
 ]
 
 
@@ -92,13 +94,15 @@ class Request(ctypes.Structure):
     """hc_request: one served request."""
     _fields_ = [("table", ctypes.c_int32), ("op", ctypes.c_int32), ("h_keys", ctypes.c_void_p),
                 ("h_vals", ctypes.c_void_p), ("n", ctypes.c_int64), ("h_status", ctypes.c_void_p),
-                ("h_vals_out", ctypes.c_void_p), ("arrival", ctypes.c_double), ("done", ctypes.c_double)]
+                ("h_vals_out", ctypes.c_void_p), ("arrival", ctypes.c_double), ("deadline", ctypes.c_double),
+                ("done", ctypes.c_double), ("rc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ServeStats(ctypes.Structure):
     """hc_serve_stats."""
     _fields_ = [("requests", ctypes.c_int64), ("ops", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("queued_max", ctypes.c_int64), ("wall_s", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("queued_max", ctypes.c_int64), ("timed_out", ctypes.c_int64), ("wall_s", ctypes.c_double),
+                ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("p999_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
 
 
@@ -147,6 +151,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "hc_unpack_short3": (i32, [vp, i64, vp, vp]),
         "hc_server_create": (i32, [P(vp), P(vp), i32, P(ServeConfig)]),
         "hc_server_run": (i32, [vp, P(Request), i64, i32, ctypes.c_double, P(ServeStats)]),
+        "hc_server_start": (i32, [vp]),
+        "hc_server_submit": (i32, [vp, P(Request)]),
+        "hc_server_wait": (i32, [vp, P(Request), ctypes.c_double]),
+        "hc_server_stop": (i32, [vp, P(ServeStats)]),
         "hc_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():

@@ -164,3 +164,124 @@ def test_served_against_oracle(merge):
     srv.close()
     for tab in tabs:
         tab.close()
+
+
+def _expected(slots, pre, reqs_by_table):
+    with cf.ThreadPoolExecutor(16) as ex:
+        return list(ex.map(_oracle_replay, [(slots, pre[t], reqs_by_table[t]) for t in range(len(pre))]))
+
+
+def _check_against(reqs, expected, tabs):
+    for r in reqs:
+        if r.rc != L.OK:
+            continue
+        exp = expected[r.table][0][r.rid]
+        if r.op == L.OP_FIND:
+            C.assert_find(r.status, r.values, exp[0], exp[1], f"request {r.rid} find")
+        else:
+            C.assert_status(r.keys.numpy(), r.status, exp, f"request {r.rid} op {r.op}")
+    for t, tab in enumerate(tabs):
+        gk, gv = tab.dump_numpy()
+        ok, ov = expected[t][1]
+        C.assert_contents(gk, gv, ok, ov, f"table {t} contents")
+
+
+@pytest.mark.parametrize("merge", [True, False])
+def test_live_submissions_from_two_threads_against_oracle(merge):
+    """The server's own loop (hc_server_start) fed by two host threads at once
+    (each submitting the requests of its own half of the tables, so a table's
+    arrival order is its thread's order), with requests up to 5x a launch
+    slot (cut into chunks); every result and the final contents against the
+    oracle's replay of each table in that order."""
+    import threading
+    from paper_1908_05936_gb300 import build
+    build.build()
+    n_tables, slots, prefill = 8, 1 << 20, 1 << 19
+    spec = recipes.served_requests(160, n_tables, 1.0, seed=21, max_log2=17)
+    cdf = recipes.zipf_cdf(1 << 20)
+    pre = [splitmix.stream_u64(7100 + t, 0, 0, prefill) for t in range(n_tables)]
+    tabs = []
+    for t in range(n_tables):
+        tab = Table(L.MAP_U64_U64, slots, bucket_bytes=64)
+        tab.insert(torch.from_numpy(pre[t].view(np.int64)).cuda(),
+                   torch.from_numpy(splitmix.value_of(pre[t]).view(np.int64)).cuda(), status=False)
+        tabs.append(tab)
+    torch.cuda.synchronize()
+    reqs, per_table = [], [[] for _ in range(n_tables)]
+    for q in spec:
+        k = recipes.zipf_keys(q.table, q.key_stream, q.n, cdf)
+        v = splitmix.value_of(k) if q.op == L.OP_INSERT else None
+        reqs.append(ServedRequest(q.rid, q.table, q.op, torch.from_numpy(k.view(np.int64)).pin_memory(),
+                                  torch.from_numpy(v.view(np.int64)).pin_memory() if v is not None else None))
+        per_table[q.table].append((q.rid, q.op, k, v))
+    srv = Server(tabs, slot_bytes=1 << 19, lanes=4, depth=2, merge=merge, max_items=8)
+    assert max(q.n for q in spec) * 25 > 5 * (1 << 19)        # some requests need several slots
+    srv.start()
+    errors = []
+
+    def feed(parity):
+        try:
+            mine = [r for r in reqs if r.table % 2 == parity]
+            for i, r in enumerate(mine):
+                srv.submit(r)
+                if i % 7 == 6:
+                    srv.wait(mine[i - 3])                      # interleave waiting with submitting
+        except Exception as e:                                 # reported by the main thread
+            errors.append(e)
+
+    th = [threading.Thread(target=feed, args=(p,)) for p in (0, 1)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errors, errors
+    for r in reqs:
+        assert srv.wait(r) == L.OK and r.rc == L.OK
+    stats = srv.stop()
+    assert stats["requests"] == len(reqs) and stats["timed_out"] == 0
+    _check_against(reqs, _expected(slots, pre, per_table), tabs)
+    srv.close()
+    for tab in tabs:
+        tab.close()
+
+
+def test_deadline_drops_only_the_late_request():
+    """One slot per lane, busy with a large request cut into many chunks;
+    requests with a short deadline queued behind it on the same table are
+    dropped (HC_ERR_TIMEOUT, nothing of them runs), the others are served,
+    and everything that ran matches the oracle."""
+    from paper_1908_05936_gb300 import build
+    build.build()
+    slots = 1 << 22
+    pre = [splitmix.stream_u64(7200, 0, 0, 1 << 20)]
+    tab = Table(L.MAP_U64_U64, slots, bucket_bytes=64)
+    tab.insert(torch.from_numpy(pre[0].view(np.int64)).cuda(),
+               torch.from_numpy(splitmix.value_of(pre[0]).view(np.int64)).cuda(), status=False)
+    torch.cuda.synchronize()
+
+    def req(rid, op, keys, deadline=0.0):
+        v = splitmix.value_of(keys) if op == L.OP_INSERT else None
+        return ServedRequest(rid, 0, op, torch.from_numpy(keys.view(np.int64)).pin_memory(),
+                             torch.from_numpy(v.view(np.int64)).pin_memory() if v is not None else None,
+                             deadline=deadline)
+
+    big = req(0, L.OP_INSERT, splitmix.stream_u64(7201, 0, 0, 1 << 21))          # about 50 chunks of 1 MiB
+    late = [req(1 + i, L.OP_INSERT, splitmix.stream_u64(7300 + i, 0, 0, 1000), deadline=1e-4) for i in range(3)]
+    calm = req(4, L.OP_FIND, np.concatenate([pre[0][:500], late[0].keys.numpy().view(np.uint64)[:500]]))
+    srv = Server([tab], slot_bytes=1 << 20, lanes=1, depth=1, merge=True)
+    srv.start()
+    for r in [big] + late + [calm]:
+        srv.submit(r)
+    assert srv.wait(big) == L.OK
+    for r in late:
+        assert srv.wait(r) == L.ERR_TIMEOUT and r.rc == L.ERR_TIMEOUT
+    assert srv.wait(calm) == L.OK
+    stats = srv.stop()
+    assert stats["timed_out"] == 3 and stats["requests"] == 2
+    per_table = [[(r.rid, r.op, r.keys.numpy().view(np.uint64), splitmix.value_of(r.keys.numpy().view(np.uint64))
+                   if r.op == L.OP_INSERT else None) for r in (big, calm)]]
+    exp = _expected(slots, pre, per_table)
+    _check_against([big, calm] + late, exp, [tab])
+    assert int(calm.status[500:].sum()) == 0                     # the dropped inserts never reached the table
+    srv.close()
+    tab.close()

@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.hc_abi_version() == 1
+    assert lib.hc_abi_version() == 2
 
 
 def test_argument_errors_before_any_launch(lib):
@@ -116,8 +116,8 @@ def test_struct_layouts_match_the_header(tmp_path):
               "hc_device_view": (L.DeviceView, ["nb", "kind", "pad_from"]),
               "hc_predicate": (L.Predicate, ["lo", "box"]),
               "hc_serve_config": (L.ServeConfig, ["slot_bytes", "batch"]),
-              "hc_request": (L.Request, ["h_keys", "n", "arrival", "done"]),
-              "hc_serve_stats": (L.ServeStats, ["wall_s", "max_ms"])}
+              "hc_request": (L.Request, ["h_keys", "n", "arrival", "deadline", "done", "rc"]),
+              "hc_serve_stats": (L.ServeStats, ["timed_out", "wall_s", "max_ms"])}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hc.h"', "int main(void) {"]
     for name, (_, fields) in checks.items():
         lines.append(f'    printf("%zu\\n", sizeof({name}));')
