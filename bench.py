@@ -40,7 +40,7 @@ BYTES_PER_OP = {"insert": 16 + 1 + 32 + 32, "find": 8 + 8 + 1 + 32, "erase": 8 +
 # they inserted; `requests_per_op` the same for lts__t_requests_srcunit_tex.sum
 # (requests from the SMs to L2).  Valid only while the kernel sources hash to
 # `digest`.
-INSERT_TRAFFIC = {"bytes_per_op": 227.68, "requests_per_op": 3.547, "digest": "2dc36df6c4a95205"}
+INSERT_TRAFFIC = {"bytes_per_op": 227.7, "requests_per_op": 3.545, "digest": "778943ff0af1f86f"}
 
 
 def insert_kernel_digest() -> str:
@@ -84,7 +84,8 @@ def parse():
                     help="default workload only: skip the batched, served, RGB-D and set<u32> comparisons")
     ap.add_argument("--cpu-sample-log2", type=int, default=24)
     ap.add_argument("--workload", default="map_sweep",
-                    choices=["map_sweep", "map_grid", "device_api", "multi_table", "served", "rgbd", "set_u32"])
+                    choices=["map_sweep", "map_grid", "device_api", "multi_table", "served", "rgbd", "set_u32",
+                             "read_ceiling"])
     ap.add_argument("--rgbd-slots", type=int, default=12_500_000)
     ap.add_argument("--rgbd-hash", type=int, default=1,
                     help="1 = the paper's spatial hash on packed 21-bit coordinates, 2 = on short3 keys, 0 = mix64")
@@ -563,6 +564,32 @@ def random_read_ceiling(torch, L):
             "note": "each random read moves one 128-byte line from HBM on this GPU"}
 
 
+def run_read_ceiling(args):
+    """Calibration: the rate of random 32-byte reads (hc_measure_random_reads,
+    2^26 reads per launch, five launches after one warm-up) over buffers from
+    8 MiB (inside L2) to 16 GiB.  Beyond L2 it is the ceiling of a
+    probe-bound operation."""
+    import ctypes
+    import torch
+    from paper_1908_05936_gb300 import _lib as L
+    from paper_1908_05936_gb300 import build
+    build.build()
+    rows = []
+    for mib in (8, 32, 64, 96, 128, 256, 512, 1024, 2048, 4096, 8192, 16384):
+        buf = torch.empty(mib << 20, dtype=torch.uint8, device="cuda")
+        ms = ctypes.c_float()
+        n = 1 << 26
+        L.check(L.load().hc_measure_random_reads(buf.data_ptr(), buf.numel(), n, 5, ctypes.byref(ms),
+                                                 torch.cuda.current_stream().cuda_stream))
+        del buf
+        torch.cuda.empty_cache()
+        rows.append({"buffer_mib": mib, "g_reads_per_s": round(n / (ms.value * 1e-3) / 1e9, 2)})
+    return {"metric": "random 32-byte reads per second by buffer size", "value": rows[9]["g_reads_per_s"],
+            "unit": "G reads/s (4 GiB)", "n_gpus": 1, "higher_is_better": True, "dtype": "u8",
+            "data": "synthetic (pseudo-random offsets)", "config": {"workload": "calibration, 2^26 reads per launch"},
+            "sweep": rows}
+
+
 def hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -974,7 +1001,7 @@ def run_served(args):
     First each form serves every request as fast as it can (its capacity:
     the median of three passes after an untimed one); then both serve
     real-time arrivals at 50 %, 80 % and 100 % of the plain path's capacity,
-    three runs each (the run with the median p99 reported)."""
+    five runs each (medians over the runs reported)."""
     import torch
     from paper_1908_05936_gb300 import _lib as L
     from paper_1908_05936_gb300 import build
@@ -1025,17 +1052,18 @@ def run_served(args):
     cap = capacity(plain)
     cap_rate = cap["requests"] / cap["wall_s"]
     cap_merged = capacity(merged)
-    # each load point three times per form, alternating; the run with the
-    # median p99 is reported (a p99 of 3000 requests rests on 30 of them)
+    # each load point five times per form, alternating; p50, p99 and Mops/s
+    # are the medians over the runs (a p99 of 3000 requests rests on 30 of
+    # them, and the single host thread of the loop shares the host)
     def median_run(runs):
-        runs = sorted(runs, key=lambda r: r["p99_ms"])
-        return dict(runs[len(runs) // 2], p99_runs=[r["p99_ms"] for r in runs],
-                    p50_runs=sorted(r["p50_ms"] for r in runs))
+        med = lambda k: statistics.median(r[k] for r in runs)
+        return dict(runs[0], p50_ms=med("p50_ms"), p99_ms=med("p99_ms"), mops=med("mops"),
+                    p99_runs=sorted(r["p99_ms"] for r in runs), p50_runs=sorted(r["p50_ms"] for r in runs))
     loads = {}
     for frac in (0.5, 0.8, 1.0):
         rate = frac * cap_rate
         runs = {"plain": [], "merged": []}
-        for _ in range(3):
+        for _ in range(5):
             runs["plain"].append(plain.run(requests(rate), realtime=True))
             runs["merged"].append(merged.run(requests(rate), realtime=True))
         loads[f"{int(frac * 100)}%"] = {"rate_req_per_s": round(rate, 1), "plain": median_run(runs["plain"]),
@@ -1129,6 +1157,9 @@ def main():
         return
     if args.workload == "map_grid":
         print(json.dumps(run_map_grid(args)))
+        return
+    if args.workload == "read_ceiling":
+        print(json.dumps(run_read_ceiling(args)))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -140,7 +140,9 @@ typedef struct hc_stats_t {
     int64_t capacity;        /* slots, as requested at create / rehash       */
     int64_t slot_bytes;      /* bytes per slot: key plus value                */
     int64_t table_bytes;     /* device bytes held by the table               */
-    uint32_t error_bits;     /* 1 = an insert overflowed, 2 = probe bound hit */
+    uint32_t error_bits;     /* 1 = an insert overflowed, 2 = probe bound hit,
+                                4 = a bounds check of the debug build failed
+                                (a build with -DHC_DEBUG only)                */
     uint32_t reserved;
 } hc_stats_t;
 
@@ -460,7 +462,9 @@ HC_API hc_rc hc_batch_run(const hc_batch_item *items, int64_t n_items, const hc_
  * every GPU that loads the library holds until the process exits.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: after cudaDeviceReset (a new primary context) the library
+ *     must be loaded again before this call is used.
  *   - Every call shares the array; the counters are reset by each call, the
  *     descriptors are overwritten.  Calls whose work overlaps on the GPU (on
  *     different streams, or several host threads) race on the array and give
@@ -476,18 +480,19 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
  * request is one insert / find / erase of a host key array on one table.
  * The loop:
  *   1. an arrived request joins its table's FIFO; a table belongs to one lane
- *      (a CUDA stream, table index mod lanes), so its requests reach the GPU
- *      in arrival order;
- *   2. each lane owns `depth` launch slots; a slot is a device staging buffer
- *      of slot_bytes (keys, values, results) with pinned host staging of the
- *      same size and descriptor scratch -- the slots and the resident tables
- *      are the whole HBM budget;
- *   3. a free slot takes the heads of its lane's FIFOs, one per table, while
- *      they fit (at most max_items), copies their inputs host->device (small
- *      requests packed into one copy), runs one hc_batch_run over them
- *      (merge = 1; a slot holding a single request runs its range call
- *      instead) or one range call each (merge = 0), copies the results
- *      device->host and records an event;
+ *      (table index mod lanes);
+ *   2. each lane owns `depth` launch slots; a slot is a CUDA stream of its
+ *      own, a device staging buffer of slot_bytes (keys, values, results)
+ *      with pinned host staging of the same size, and descriptor scratch --
+ *      the slots and the resident tables are the whole HBM budget;
+ *   3. a free slot takes the heads of its lane's FIFOs, one per table and only
+ *      of tables with nothing in another slot (so a table's requests run in
+ *      arrival order), while they fit (at most max_items); with merge = 1 it
+ *      takes either small requests (up to 65536 keys), run as one
+ *      hc_batch_run (or as the range call of a lone one), or one large
+ *      request, run as its range call; with merge = 0 one request.  It
+ *      copies the inputs host->device (small requests packed into one copy),
+ *      launches, copies the results device->host and records an event;
  *   4. a finished slot hands each request its results and completion time.
  * A request larger than a slot is cut into chunks that fit, run one after
  * another before the table's next request; each chunk is one concurrent
@@ -505,7 +510,7 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
 typedef struct hc_server hc_server;
 
 typedef struct hc_serve_config {
-    int32_t lanes;           /* streams (default 4)                              */
+    int32_t lanes;           /* groups of tables sharing slots (default 4)       */
     int32_t depth;           /* launch slots per lane (default 2)                */
     int64_t slot_bytes;      /* device (and pinned host) bytes per slot (default 64 MiB, at least 64 KiB) */
     int32_t merge;           /* 1: one batched launch per slot; 0: one call per request */

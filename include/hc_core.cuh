@@ -51,7 +51,7 @@ namespace hc {
 
 enum : int { KIND_SET_U32 = 0, KIND_SET_U64 = 1, KIND_MAP_I64_I32 = 2, KIND_MAP_U64_U64 = 3 };
 enum : uint32_t { ST_INSERTED = 0, ST_EXISTS = 1, ST_OVERFLOW = 2, ST_ERASED = 3, ST_NOT_FOUND = 4 };
-enum : uint32_t { ERR_OVERFLOW = 1u, ERR_PROBE_BOUND = 2u };
+enum : uint32_t { ERR_OVERFLOW = 1u, ERR_PROBE_BOUND = 2u, ERR_DEBUG_BOUNDS = 4u };
 enum : int { HASH_MIX64 = 0, HASH_TESCHNER = 1, HASH_TESCHNER_SHORT3 = 2 };
 
 // Restarts of an insert probe after lost compare-and-swap races.  Each lost
@@ -163,6 +163,41 @@ __device__ __forceinline__ unsigned long long next_bucket(const View &v, unsigne
     return b == v.nb ? 0ull : b;
 }
 
+// Debug bounds build (-DHC_DEBUG): an index outside the table, or a key
+// range outside the caller's array, records ERR_DEBUG_BOUNDS in the table
+// header; a bad bucket or slot is replaced by bucket 0, slot 0, so nothing is
+// accessed out of bounds and nothing traps.  The normal build compiles the
+// checks away.
+__device__ __forceinline__ void debug_bucket(const View &v, unsigned long long &b) {
+#ifdef HC_DEBUG
+    if (b >= v.nb) {
+        atomicOr(&v.hdr->err, ERR_DEBUG_BOUNDS);
+        b = 0;
+    }
+#else
+    (void)v;
+    (void)b;
+#endif
+}
+
+__device__ __forceinline__ void debug_range(const View &v, long long first, long long count, long long n) {
+#ifdef HC_DEBUG
+    if (first < 0 || count < 0 || first + count > n) atomicOr(&v.hdr->err, ERR_DEBUG_BOUNDS);
+#else
+    (void)v;
+    (void)first;
+    (void)count;
+    (void)n;
+#endif
+}
+
+// Address of bucket b (checked in the debug build).
+template <int BB>
+__device__ __forceinline__ unsigned char *bucket_at(const View &v, unsigned long long b) {
+    debug_bucket(v, b);
+    return v.buckets + b * BB;
+}
+
 // --------------------------------------------------------------- memory ---
 
 // One lane's share of a bucket: LB bytes in 32-byte vector loads cached in L2
@@ -211,10 +246,21 @@ template <int KIND, int BB> struct Slots {
     static constexpr int KRB = SPB * KB;                                 // key region bytes
     static_assert(KRB + SPB * VB <= BB, "bucket overflow");
     __device__ __forceinline__ static unsigned char *key(const View &v, unsigned long long b, int s) {
+        check(v, b, s);
         return v.buckets + b * BB + (size_t)s * KB;
     }
     __device__ __forceinline__ static unsigned char *val(const View &v, unsigned long long b, int s) {
+        check(v, b, s);
         return v.buckets + b * BB + KRB + (size_t)s * VB;
+    }
+    __device__ __forceinline__ static void check(const View &v, unsigned long long &b, int &s) {
+        debug_bucket(v, b);
+#ifdef HC_DEBUG
+        if (s < 0 || s >= SPB) {
+            atomicOr(&v.hdr->err, ERR_DEBUG_BOUNDS);
+            s = 0;
+        }
+#endif
     }
 };
 
@@ -407,7 +453,7 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.buckets + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(bucket_at<BB>(v, b[j]) + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;
@@ -522,7 +568,7 @@ __device__ __forceinline__ void find_group(const View &v, const typename Traits<
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.buckets + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(bucket_at<BB>(v, b[j]) + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;
@@ -580,7 +626,7 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
         LaneWords<LB> lw[KPT];
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
-            if (active >> j & 1u) lw[j].load(v.buckets + b[j] * BB + grp.sub * LB);
+            if (active >> j & 1u) lw[j].load(bucket_at<BB>(v, b[j]) + grp.sub * LB);
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             if (!(active >> j & 1u)) continue;

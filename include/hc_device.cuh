@@ -118,7 +118,7 @@ __device__ __forceinline__ void scan(const View &v, unsigned long long b, typena
                                      uint32_t &match, uint32_t &empty) {
     using S = hc::Slots<KIND, BB>;
     hc::LaneWords<S::KRB> lw;
-    lw.load(v.buckets + b * BB);
+    lw.load(hc::bucket_at<BB>(v, b));
     match = 0;
     empty = 0;
 #pragma unroll

@@ -11,7 +11,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhc.so")
+# HC_LIBRARY selects another build of the same library (the debug bounds
+# build, libhc_debug.so); it must exist like the default one.
+LIB_PATH = os.environ.get("HC_LIBRARY") or os.path.join(HERE, "libhc.so")
 
 # hc_kind
 SET_U32, SET_U64, MAP_I64_I32, MAP_U64_U64 = 0, 1, 2, 3

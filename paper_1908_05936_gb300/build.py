@@ -19,6 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhc.so")
 EXAMPLES_SRC = os.path.join(HERE, "examples", "device_api.cu")
 EXAMPLES_LIB = os.path.join(HERE, "libhc_examples.so")
+DEBUG_LIB = os.path.join(HERE, "libhc_debug.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -55,8 +56,8 @@ def stale(lib: str = LIB) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, extra: list[str], build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -79,25 +80,37 @@ def build_examples(force: bool = False, verbose: bool = False) -> str:
     return EXAMPLES_LIB
 
 
-def build(force: bool = False, extra: list[str] | None = None, verbose: bool = False) -> str:
-    """Compile and link libhc.so next to this file; returns its path."""
-    if not force and not stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, extra: list[str] | None = None, verbose: bool = False, lib: str = LIB) -> str:
+    """Compile and link libhc.so (or `lib`, with `extra` nvcc flags) next to
+    this file; returns its path."""
+    if not force and not stale(lib):
+        return lib
+    build_dir = BUILD if lib == LIB else os.path.join(BUILD, os.path.splitext(os.path.basename(lib))[0])
+    os.makedirs(build_dir, exist_ok=True)
     extra = extra or []
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), SOURCES))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}")
-    return LIB
+        print(f"built {lib}")
+    return lib
+
+
+def build_debug(force: bool = False, verbose: bool = False) -> str:
+    """libhc_debug.so: the same library with the debug bounds checks
+    (-DHC_DEBUG): every bucket and slot index is checked against the table and
+    every key range against its call; a violation sets error bit 4 of the
+    table header (hc_stats, hc_status) instead of faulting."""
+    return build(force=force, extra=["-DHC_DEBUG"], verbose=verbose, lib=DEBUG_LIB)
 
 
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True)
     build_examples(force="--force" in sys.argv, verbose=True)
+    if "--debug" in sys.argv:
+        build_debug(force="--force" in sys.argv, verbose=True)

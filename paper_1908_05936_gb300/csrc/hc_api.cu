@@ -494,6 +494,7 @@ hc_rc hc_status(hc_table *t, void *stream) {
         HC_CUDA(cudaGetLastError(), "clearing the error bits");
         HC_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "synchronising the stream");
     }
+    if (st.error_bits & hc::ERR_DEBUG_BOUNDS) return fail(HC_ERR_STATE, "a debug bounds check failed");
     if (st.error_bits & hc::ERR_PROBE_BOUND) return fail(HC_ERR_STATE, "a device-side probe bound was reached");
     if (st.error_bits & hc::ERR_OVERFLOW) return fail(HC_ERR_OVERFLOW, "an insert found the table full");
     return HC_OK;

@@ -84,6 +84,7 @@ k_batch_phase(const BatchItemDev *__restrict__ items, int n_items, long long n_c
         const BatchItemDev it = items[lo];
         const long long k0 = ((long long)c - it.chunk_begin) * tile;
         const long long k1 = k0 + tile < it.n ? k0 + tile : it.n;
+        debug_range(it.v, k0, k1 - k0, it.n);
         run_chunk<KIND, OP, BB, LB, KPT>(it, k0, k1);
     }
 }
@@ -117,6 +118,7 @@ k_batch_stream(const BatchItemDev *__restrict__ items, int n_items, long long n_
         const auto *keys = (const typename T::Key *)it.keys;
         for (long long p0 = k0; p0 < k1; p0 += piece) {
             const int m = (int)(k1 - p0 < piece ? k1 - p0 : piece);
+            debug_range(it.v, p0, m, it.n);
             if constexpr (OP == OP_INSERT)
                 insert_stream_chunk<KIND, BB, KPT, S>(it.v, keys, (const typename T::Val *)it.vals, p0, m, it.out,
                                                       nullptr);

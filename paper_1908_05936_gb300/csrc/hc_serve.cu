@@ -39,6 +39,7 @@ namespace {
 constexpr uint32_t kServerMagic = 0x48435356u;   // "HCSV"
 constexpr int64_t kPackLimit = 1 << 16;          // units up to this many keys are packed into one copy
 constexpr int32_t kPending = -1;                 // hc_request.rc while a request is queued or running
+constexpr size_t nt_none = ~(size_t)0;
 
 hc_rc sfail(hc_rc rc, const std::string &msg) { return hc_internal_fail(rc, msg.c_str()); }
 
@@ -78,6 +79,7 @@ bool page_locked(const void *p) {
 
 struct Slot {
     int lane = 0;
+    cudaStream_t stream = nullptr;     // each slot has a stream of its own
     unsigned char *d_buf = nullptr;    // device staging
     unsigned char *h_in = nullptr;     // pinned host staging of packed inputs
     unsigned char *h_out = nullptr;    // pinned host staging of outputs
@@ -174,7 +176,7 @@ bool outputs_locked(const hc_server *s, const hc_request &r) {
 }
 
 hc_rc launch(hc_server *s, Slot &sl, std::vector<Track> &tr, const std::vector<Unit> &batch) {
-    cudaStream_t st = s->streams[sl.lane];
+    cudaStream_t st = sl.stream;
     sl.placed.clear();
     int64_t off = 0, packed_end = 0;
     for (const Unit &u : batch) {
@@ -303,6 +305,7 @@ hc_rc serve_loop(hc_server *srv, const Source &src, double timeout_s, hc_serve_s
     std::vector<std::vector<int>> lane_tables((size_t)srv->lanes);
     for (int t = 0; t < n_tables; ++t) lane_tables[(size_t)(t % srv->lanes)].push_back(t);
     std::vector<size_t> rr((size_t)srv->lanes, 0);
+    std::vector<int> inflight((size_t)n_tables, 0);   // units of each table in a slot (at most one)
     std::vector<Track> tr;
     tr.reserve(src.live ? 1024 : (size_t)src.n_reqs);
     int64_t next = 0, n_admitted = 0, n_done = 0, n_timed_out = 0, launches = 0, queued = 0, queued_max = 0, ops = 0;
@@ -384,6 +387,7 @@ hc_rc serve_loop(hc_server *srv, const Source &src, double timeout_s, hc_serve_s
             for (const Placed &p : sl.placed) {
                 Track &t = tr[(size_t)p.u.req];
                 const hc_request &r = *t.r;
+                --inflight[(size_t)r.table];
                 if (!p.direct_out && p.u.n > 0) {
                     const int vb = val_bytes(srv->tables[r.table]->kind);
                     if (r.h_status) std::memcpy(r.h_status + p.u.off, sl.h_out + p.o_off, (size_t)p.u.n);
@@ -415,29 +419,45 @@ hc_rc serve_loop(hc_server *srv, const Source &src, double timeout_s, hc_serve_s
                 }
             }
         }
-        // dispatch: a free slot takes the head units of its lane's tables
+        // dispatch: a free slot takes head units of its lane's tables.  A
+        // table has at most one unit in a slot, so its units run in FIFO
+        // order although slots run on streams of their own.  In merged mode
+        // small units (up to kPackLimit keys) share a launch; a large unit
+        // runs alone, so small requests never wait for a large one in the
+        // same launch.
         for (Slot &sl : srv->slots) {
             if (sl.busy) continue;
             const std::vector<int> &tabs = lane_tables[(size_t)sl.lane];
             if (tabs.empty()) continue;
             batch.clear();
             int64_t used = 256;
+            int mode = 0;                     // 1: small units merged, 2: one large unit
+            size_t skipped = nt_none;         // first large head passed over by a merged launch
             const size_t nt = tabs.size();
-            for (size_t j = 0; j < nt && (int)batch.size() < srv->max_items; ++j) {
+            for (size_t j = 0; j < nt && (int)batch.size() < srv->max_items && mode != 2; ++j) {
                 const int t = tabs[(rr[(size_t)sl.lane] + j) % nt];
-                if (fifo[(size_t)t].empty()) continue;
+                if (fifo[(size_t)t].empty() || inflight[(size_t)t]) continue;
                 const Unit u = fifo[(size_t)t].front();
+                const bool large = u.n > kPackLimit;
+                if (srv->merge && mode == 1 && large) {
+                    if (skipped == nt_none) skipped = j;
+                    continue;
+                }
                 int64_t in, out;
                 need(srv, *tr[(size_t)u.req].r, u.n, &in, &out);
                 if (used + in + out > srv->slot_bytes) continue;
+                mode = large ? 2 : 1;
                 batch.push_back(u);
                 fifo[(size_t)t].pop_front();
+                ++inflight[(size_t)t];
                 Track &k = tr[(size_t)u.req];
                 if (k.dispatched++ == 0) --queued;
                 used += in + out;
             }
             if (batch.empty()) continue;
-            rr[(size_t)sl.lane] = (rr[(size_t)sl.lane] + 1) % nt;
+            // the lane's next slot starts at a large head this launch passed
+            // over, so small requests cannot keep it waiting
+            rr[(size_t)sl.lane] = (rr[(size_t)sl.lane] + (skipped != nt_none ? skipped : 1)) % nt;
             const hc_rc rc = launch(srv, sl, tr, batch);
             if (rc != HC_OK) return rc;
             ++launches;
@@ -493,14 +513,13 @@ hc_rc hc_server_create(hc_server **out, hc_table *const *tables, int32_t n_table
     s->batch = c.batch;
     const int64_t desc_bytes = hc_batch_scratch_bytes(s->max_items);
     cudaError_t e = cudaGetDevice(&s->device);
-    for (int l = 0; l < s->lanes && e == cudaSuccess; ++l) {
+    s->slots.resize((size_t)(s->lanes * s->depth));
+    for (size_t i = 0; i < s->slots.size() && e == cudaSuccess; ++i) {
         cudaStream_t st = nullptr;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         s->streams.push_back(st);
-    }
-    s->slots.resize((size_t)(s->lanes * s->depth));
-    for (size_t i = 0; i < s->slots.size() && e == cudaSuccess; ++i) {
         Slot &sl = s->slots[i];
+        sl.stream = st;
         sl.lane = (int)(i / (size_t)s->depth);
         sl.desc_bytes = desc_bytes;
         e = cudaMalloc(&sl.d_buf, (size_t)s->slot_bytes);

@@ -146,7 +146,7 @@ __device__ __forceinline__ void find_stream_chunk(const View &v, const typename 
         LaneWords<LB> lw[S];
 #pragma unroll
         for (int s = 0; s < S; ++s)
-            if (active >> s & 1u) load_find<LB>(lw[s], v.buckets + b[s] * BB);
+            if (active >> s & 1u) load_find<LB>(lw[s], bucket_at<BB>(v, b[s]));
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             if (!(active >> s & 1u)) continue;
@@ -190,7 +190,9 @@ k_find_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8
               typename Traits<KIND>::Val *vals_out) {
     const long long chunk = (long long)blockDim.x * KPT;
     const long long c0 = (long long)blockIdx.x * chunk;
-    find_stream_chunk<KIND, BB, KPT, S>(v, keys, c0, (int)(n - c0 < chunk ? n - c0 : chunk), found, vals_out);
+    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    debug_range(v, c0, m, n);
+    find_stream_chunk<KIND, BB, KPT, S>(v, keys, c0, m, found, vals_out);
 }
 
 // Streaming map lookup by lane pairs: the two lanes of a pair handle one key.
@@ -270,7 +272,7 @@ k_find_pair(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t
         for (int s = 0; s < S; ++s) {
             if (!(active >> s & 1u)) continue;
             const unsigned long long bb = (odd && !first[s]) ? next_bucket(v, b[s]) : b[s];
-            load_find<HB>(lw[s], v.buckets + bb * BB + ((odd && first[s]) ? HB : 0));
+            load_find<HB>(lw[s], bucket_at<BB>(v, bb) + ((odd && first[s]) ? HB : 0));
         }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -414,7 +416,7 @@ __device__ __forceinline__ void insert_stream_chunk(const View &v, const typenam
         LaneWords<LB> lw[S];
 #pragma unroll
         for (int s = 0; s < S; ++s)
-            if (active >> s & 1u) lw[s].load(v.buckets + b[s] * BB);
+            if (active >> s & 1u) lw[s].load(bucket_at<BB>(v, b[s]));
         uint32_t claiming = 0;
         uint32_t finished = 0;
 #pragma unroll
@@ -509,7 +511,9 @@ k_insert_stream(View v, const typename Traits<KIND>::Key *keys, const typename T
                 uint8_t *status, const uint8_t *skip) {
     const long long chunk = (long long)blockDim.x * KPT;
     const long long c0 = (long long)blockIdx.x * chunk;
-    insert_stream_chunk<KIND, BB, KPT, S>(v, keys, vals, c0, (int)(n - c0 < chunk ? n - c0 : chunk), status, skip);
+    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    debug_range(v, c0, m, n);
+    insert_stream_chunk<KIND, BB, KPT, S>(v, keys, vals, c0, m, status, skip);
 }
 
 // Streaming erase: the staging and refilling of k_find_stream; a slot that
@@ -575,7 +579,7 @@ __device__ __forceinline__ void erase_stream_chunk(const View &v, const typename
         LaneWords<LB> lw[S];
 #pragma unroll
         for (int s = 0; s < S; ++s)
-            if (active >> s & 1u) lw[s].load(v.buckets + b[s] * BB);
+            if (active >> s & 1u) lw[s].load(bucket_at<BB>(v, b[s]));
         uint32_t hitting = 0, finished = 0;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -628,7 +632,9 @@ __global__ void __launch_bounds__(256, HC_STREAM_ERASE_MINB)
 k_erase_stream(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t *status, const uint8_t *skip) {
     const long long chunk = (long long)blockDim.x * KPT;
     const long long c0 = (long long)blockIdx.x * chunk;
-    erase_stream_chunk<KIND, BB, KPT, S>(v, keys, c0, (int)(n - c0 < chunk ? n - c0 : chunk), status, skip);
+    const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
+    debug_range(v, c0, m, n);
+    erase_stream_chunk<KIND, BB, KPT, S>(v, keys, c0, m, status, skip);
 }
 
 }  // namespace hc

@@ -109,6 +109,7 @@ class Pair:
 
     def check(self):
         assert self.g.size() == self.o.size(), (self.g.size(), self.o.size())
+        assert not self.g.stats()["error_bits"] & 4, "a bounds check of the debug build failed"
         gk, gv = self.g.dump_numpy()
         ok, ov = self.o.dump()
         C.assert_contents(gk, gv, ok, ov)

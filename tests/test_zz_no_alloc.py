@@ -58,12 +58,16 @@ def _item_array(items):
     return arr
 
 
-def test_noalloc_matches_batch_on_two_calls():
+@pytest.mark.parametrize("kpt,block", [(1, 256), (4, 128)], ids=["lock-step", "streaming"])
+def test_noalloc_matches_batch_on_two_calls(kpt, block):
+    """Same shape on both entry points: the lock-step phases, and the
+    streaming phases with their dynamic shared memory."""
     ops, ((tab_a, items_a, outs_a), (tab_b, items_b, outs_b)) = _setup(seed=7)
     lib = L.load()
-    batch = Batch(items_a, use_graph=False)          # the existing entry point
+    batch = Batch(items_a, lane_bytes=0, keys_per_group=kpt, block=block, tile=1024,
+                  use_graph=False)                   # the existing entry point
     arr_b = _item_array(items_b)
-    cfg = L.BatchConfig(0, 1, 256, 0, 1024, 0)
+    cfg = L.BatchConfig(0, kpt, block, 0, 1024, 0)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         batch.launch()
