@@ -434,7 +434,17 @@ hc_rc serve_loop(hc_server *srv, const Source &src, double timeout_s, hc_serve_s
             int mode = 0;                     // 1: small units merged, 2: one large unit
             size_t skipped = nt_none;         // first large head passed over by a merged launch
             const size_t nt = tabs.size();
-            for (size_t j = 0; j < nt && (int)batch.size() < srv->max_items && mode != 2; ++j) {
+            // merged mode merges only when more units wait than the lane has
+            // free slots; otherwise each takes a slot of its own, as in plain
+            // mode, and nothing waits for a batched launch
+            int take = srv->max_items;
+            if (srv->merge) {
+                int free_slots = 0, waiting = 0;
+                for (const Slot &o : srv->slots) free_slots += (o.lane == sl.lane && !o.busy) ? 1 : 0;
+                for (int t : tabs) waiting += (!fifo[(size_t)t].empty() && !inflight[(size_t)t]) ? 1 : 0;
+                if (waiting <= free_slots) take = 1;
+            }
+            for (size_t j = 0; j < nt && (int)batch.size() < take && mode != 2; ++j) {
                 const int t = tabs[(rr[(size_t)sl.lane] + j) % nt];
                 if (fifo[(size_t)t].empty() || inflight[(size_t)t]) continue;
                 const Unit u = fifo[(size_t)t].front();
