@@ -40,7 +40,7 @@ BYTES_PER_OP = {"insert": 16 + 1 + 32 + 32, "find": 8 + 8 + 1 + 32, "erase": 8 +
 # they inserted; `requests_per_op` the same for lts__t_requests_srcunit_tex.sum
 # (requests from the SMs to L2).  Valid only while the kernel sources hash to
 # `digest`.
-INSERT_TRAFFIC = {"bytes_per_op": 227.7, "requests_per_op": 3.545, "digest": "778943ff0af1f86f"}
+INSERT_TRAFFIC = {"bytes_per_op": 227.7, "requests_per_op": 3.545, "digest": "28f51a8084c17ea2"}
 
 
 def insert_kernel_digest() -> str:
@@ -54,8 +54,7 @@ def insert_kernel_digest() -> str:
     stream, kernels = read("hc_stream.cuh"), read("hc_kernels.cuh")
     parts = [open(os.path.join(ROOT, "include", "hc_core.cuh")).read(),
              re.search(r"#ifndef HC_STREAM_INSERT_MINB.*?#endif", stream, re.S).group(0),
-             re.search(r"__device__ __forceinline__ void stage\(.*?\n}\n", stream, re.S).group(0),
-             re.search(r"__device__ __forceinline__ void hash_staged\(.*?\n}\n", stream, re.S).group(0),
+             re.search(r"template <class T, int KPT>\nstruct Stage \{.*?\n\};\n", stream, re.S).group(0),
              re.search(r"__device__ __forceinline__ void insert_stream_chunk\(.*?\n}\n", stream, re.S).group(0),
              re.search(r"template <int KIND, int BB, int KPT, int S>\n__global__[^\n]*\nk_insert_stream\(.*?\n}\n",
                        stream, re.S).group(0),

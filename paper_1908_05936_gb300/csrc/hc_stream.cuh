@@ -1,11 +1,11 @@
 // hc_stream.cuh -- the streaming range kernels: a block stages its chunk of
-// keys (and values) in shared memory with coalesced 16-byte loads and
-// computes every staged key's first bucket there, so neither the key load nor
-// the hash sits on a key's chain of dependent reads.  Every thread then keeps
-// S probes in flight and refills a slot from the chunk as soon as its probe
-// finishes (instead of moving its keys in lock-step rounds).  Results go to
-// shared memory and leave in coalesced stores.  One thread per key, reading
-// the bucket's key region (KRB bytes) per probe.
+// keys (and values) in shared memory with coalesced 16-byte loads, so the key
+// load leaves each key's chain of dependent reads.  Every thread then keeps S
+// probes in flight and refills a slot from the chunk as soon as its probe
+// finishes (instead of moving its keys in lock-step rounds); a key is hashed
+// when its slot takes it, while the other slots' reads are in flight.
+// Results go to shared memory and leave in coalesced stores.  One thread per
+// key, reading the bucket's key region (KRB bytes) per probe.
 #pragma once
 
 #include "hc_core.cuh"
@@ -33,40 +33,80 @@
 
 namespace hc {
 
-// Copies m elements from src (global) to dst (shared, 16-byte aligned) with
-// the whole block: 16 bytes per load where src is 16-byte aligned, element by
-// element otherwise and for the tail.
-template <class T>
-__device__ __forceinline__ void stage(T *dst, const T *src, int m) {
-    constexpr int E = 16 / (int)sizeof(T);
-    int done = 0;
-    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-        const int nv = m / E;
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-        for (int i = threadIdx.x; i < nv; i += blockDim.x) d4[i] = __ldcs(s4 + i);
-        done = nv * E;
+// The staging of one array of a block chunk (m <= blockDim.x * KPT elements)
+// into shared memory, in two steps so that a thread issues the loads of all
+// its pieces of every staged array before it stores any: load() reads
+// 16-byte pieces tid, tid + nt, ... when src is 16-byte aligned (element by
+// element otherwise, and for a tail shorter than 16 bytes) into registers;
+// store() writes them to dst (shared, 16-byte aligned), `map` applied to
+// every element on the way (the skip flags become result bytes).
+template <class T, int KPT>
+struct Stage {
+    static constexpr int E = 16 / (int)sizeof(T);          // elements per 16-byte piece
+    static constexpr int J = (KPT + E - 1) / E;            // pieces per thread
+    uint4 piece[J];
+    T elem[KPT];
+    bool vec;
+
+    __device__ __forceinline__ void load(const T *src, int m) {
+        const int nt = blockDim.x, tid = threadIdx.x;
+        vec = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+        if (vec) {
+            const int nv = m / E;
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int u = tid + j * nt;
+                if (u < nv) piece[j] = __ldcs(s4 + u);
+            }
+            const int i = nv * E + tid;                     // the tail: fewer than E elements
+            if (i < m) elem[0] = ld_stream(src + i);
+        } else {
+#pragma unroll
+            for (int j = 0; j < KPT; ++j) {
+                const int i = tid + j * nt;
+                if (i < m) elem[j] = ld_stream(src + i);
+            }
+        }
     }
-    for (int i = done + (int)threadIdx.x; i < m; i += blockDim.x) dst[i] = ld_stream(src + i);
-}
+
+    template <class F>
+    __device__ __forceinline__ void store(T *dst, int m, F map) const {
+        const int nt = blockDim.x, tid = threadIdx.x;
+        if (vec) {
+            const int nv = m / E;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int u = tid + j * nt;
+                if (u < nv) {
+                    T t[E];
+                    memcpy(t, &piece[j], 16);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) t[e] = map(t[e]);
+                    uint4 w;
+                    memcpy(&w, t, 16);
+                    reinterpret_cast<uint4 *>(dst)[u] = w;
+                }
+            }
+            const int i = nv * E + tid;
+            if (i < m) dst[i] = map(elem[0]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < KPT; ++j) {
+                const int i = tid + j * nt;
+                if (i < m) dst[i] = map(elem[j]);
+            }
+        }
+    }
+    __device__ __forceinline__ void store(T *dst, int m) const {
+        store(dst, m, [](T x) { return x; });
+    }
+};
 
 // Dynamic shared memory of the streaming kernels for a chunk of `chunk`
-// keys: per key its first bucket, key, value (vb bytes; 0 for erase) and
-// result byte.
+// keys: per key its key, value (vb bytes; 0 for erase) and result byte.
 __host__ __device__ __forceinline__ size_t stream_smem(long long chunk, int kb, int vb) {
-    return (size_t)chunk * (8 + kb + vb + 1);
-}
-
-// First buckets of the keys thread t will take (t, t + nt, ...), computed
-// right after staging, while every thread of the block does the same work.
-template <int KIND, int KPT>
-__device__ __forceinline__ void hash_staged(const View &v, const typename Traits<KIND>::Key *sk,
-                                            unsigned long long *sb, int m) {
-#pragma unroll
-    for (int j = 0; j < KPT; ++j) {
-        const int i = threadIdx.x + j * blockDim.x;
-        if (i < m) sb[i] = first_bucket(v, (unsigned long long)sk[i]);
-    }
+    return (size_t)chunk * (kb + vb + 1);
 }
 
 template <int LB>
@@ -103,15 +143,15 @@ __device__ __forceinline__ void find_stream_chunk(const View &v, const typename 
     extern __shared__ __align__(16) unsigned char smem[];
     const int nt = blockDim.x;
     const int chunk = nt * KPT;
-    unsigned long long *sb = reinterpret_cast<unsigned long long *>(smem);
-    Key *sk = reinterpret_cast<Key *>(smem + (size_t)chunk * 8);
-    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * (8 + sizeof(Key)));
-    uint8_t *sf = smem + (size_t)chunk * (8 + sizeof(Key) + sizeof(Val));
+    Key *sk = reinterpret_cast<Key *>(smem);
+    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * sizeof(Key));
+    uint8_t *sf = smem + (size_t)chunk * (sizeof(Key) + sizeof(Val));
 
+    Stage<Key, KPT> gk;
+    gk.load(keys + c0, m);
     __syncthreads();                         // the staging of a previous chunk is no longer read
-    stage(sk, keys + c0, m);
+    gk.store(sk, m);
     __syncthreads();
-    hash_staged<KIND, KPT>(v, sk, sb, m);
 
     // this thread's keys: threadIdx.x + j * nt, j < KPT
     int idx[S];
@@ -134,7 +174,7 @@ __device__ __forceinline__ void find_stream_chunk(const View &v, const typename 
             }
             idx[s] = i;
             key[s] = k;
-            b[s] = sb[i];
+            b[s] = first_bucket(v, (unsigned long long)k);
             probes[s] = 0;
             active |= 1u << s;
             return;
@@ -224,7 +264,9 @@ k_find_pair(View v, const typename Traits<KIND>::Key *keys, long long n, uint8_t
 
     const long long c0 = (long long)blockIdx.x * chunk;
     const int m = (int)(n - c0 < chunk ? n - c0 : chunk);
-    stage(sk, keys + c0, m);
+    Stage<Key, KPT> gk;
+    gk.load(keys + c0, m);
+    gk.store(sk, m);
     __syncthreads();
 
     const unsigned lane = threadIdx.x & 31;
@@ -363,18 +405,24 @@ __device__ __forceinline__ void insert_stream_chunk(const View &v, const typenam
     extern __shared__ __align__(16) unsigned char smem[];
     const int nt = blockDim.x;
     const int chunk = nt * KPT;
-    unsigned long long *sb = reinterpret_cast<unsigned long long *>(smem);
-    Key *sk = reinterpret_cast<Key *>(smem + (size_t)chunk * 8);
-    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * (8 + sizeof(Key)));
-    uint8_t *ss = smem + (size_t)chunk * (8 + sizeof(Key) + sizeof(Val));
+    Key *sk = reinterpret_cast<Key *>(smem);
+    Val *sv = reinterpret_cast<Val *>(smem + (size_t)chunk * sizeof(Key));
+    uint8_t *ss = smem + (size_t)chunk * (sizeof(Key) + sizeof(Val));
 
+    Stage<Key, KPT> gk;
+    Stage<Val, KPT> gv;
+    Stage<uint8_t, KPT> gs;
+    gk.load(keys + c0, m);
+    if constexpr (T::MAP) gv.load(vals + c0, m);
+    if (skip) gs.load(skip + c0, m);
     __syncthreads();                         // the staging of a previous chunk is no longer read
-    stage(sk, keys + c0, m);
-    if constexpr (T::MAP) stage(sv, vals + c0, m);
-    for (int i = threadIdx.x; i < m; i += nt)
-        ss[i] = (skip && ld_stream(skip + c0 + i)) ? (uint8_t)ST_EXISTS : (uint8_t)0xFF;   // 0xFF: to do
+    gk.store(sk, m);
+    if constexpr (T::MAP) gv.store(sv, m);
+    // result bytes: ST_EXISTS for keys a find reported present, 0xFF (to do)
+    if (skip) gs.store(ss, m, [](uint8_t f) { return f ? (uint8_t)ST_EXISTS : (uint8_t)0xFF; });
+    else
+        for (int i = threadIdx.x; i < m; i += nt) ss[i] = 0xFF;
     __syncthreads();
-    hash_staged<KIND, KPT>(v, sk, sb, m);
 
     Counts cnt;
     int idx[S];
@@ -402,7 +450,7 @@ __device__ __forceinline__ void insert_stream_chunk(const View &v, const typenam
             }
             idx[s] = i;
             key[s] = k;
-            b[s] = sb[i];
+            b[s] = first_bucket(v, (unsigned long long)k);
             probes[s] = 0;
             restarts[s] = 0;
             ffb[s] = ~0ull;
@@ -534,16 +582,20 @@ __device__ __forceinline__ void erase_stream_chunk(const View &v, const typename
     extern __shared__ __align__(16) unsigned char smem[];
     const int nt = blockDim.x;
     const int chunk = nt * KPT;
-    unsigned long long *sb = reinterpret_cast<unsigned long long *>(smem);
-    Key *sk = reinterpret_cast<Key *>(smem + (size_t)chunk * 8);
-    uint8_t *ss = smem + (size_t)chunk * (8 + sizeof(Key));
+    Key *sk = reinterpret_cast<Key *>(smem);
+    uint8_t *ss = smem + (size_t)chunk * sizeof(Key);
 
+    Stage<Key, KPT> gk;
+    Stage<uint8_t, KPT> gs;
+    gk.load(keys + c0, m);
+    if (skip) gs.load(skip + c0, m);
     __syncthreads();                         // the staging of a previous chunk is no longer read
-    stage(sk, keys + c0, m);
-    for (int i = threadIdx.x; i < m; i += nt)
-        ss[i] = (skip && ld_stream(skip + c0 + i)) ? (uint8_t)ST_NOT_FOUND : (uint8_t)0xFF;   // 0xFF: to do
+    gk.store(sk, m);
+    // result bytes: NOT_FOUND for the later occurrences of a key, 0xFF (to do)
+    if (skip) gs.store(ss, m, [](uint8_t f) { return f ? (uint8_t)ST_NOT_FOUND : (uint8_t)0xFF; });
+    else
+        for (int i = threadIdx.x; i < m; i += nt) ss[i] = 0xFF;
     __syncthreads();
-    hash_staged<KIND, KPT>(v, sk, sb, m);
 
     Counts cnt;
     int idx[S];
@@ -567,7 +619,7 @@ __device__ __forceinline__ void erase_stream_chunk(const View &v, const typename
             }
             idx[s] = i;
             key[s] = k;
-            b[s] = sb[i];
+            b[s] = first_bucket(v, (unsigned long long)k);
             probes[s] = 0;
             active |= 1u << s;
             return;
