@@ -67,6 +67,24 @@ def test_argument_errors_before_any_launch(lib):
     assert lib.hc_batch_destroy(None) == L.OK
 
 
+def test_served_calls_refuse_bad_handles(lib):
+    """The served loop's entry points check their handle and arguments before
+    touching the device (no GPU needed)."""
+    from paper_1908_05936_gb300 import _lib as L
+    req = L.Request(0, 0, None, None, 0, None, None, 0.0, 0.0, -1.0, -1, 0)
+    st = L.ServeStats()
+    assert lib.hc_server_create(None, None, 0, None) == L.ERR_ARG
+    h = ctypes.c_void_p()
+    assert lib.hc_server_create(ctypes.byref(h), None, 0, None) == L.ERR_ARG
+    assert lib.hc_server_start(None) == L.ERR_ARG
+    assert lib.hc_server_submit(None, ctypes.byref(req)) == L.ERR_ARG
+    assert lib.hc_server_wait(None, ctypes.byref(req), 1.0) == L.ERR_ARG
+    assert lib.hc_server_stop(None, ctypes.byref(st)) == L.ERR_ARG
+    assert lib.hc_server_run(None, ctypes.byref(req), 1, 0, 1.0, ctypes.byref(st)) == L.ERR_ARG
+    assert lib.hc_server_destroy(None) == L.OK
+    assert L.RC_NAMES[L.ERR_TIMEOUT] == "HC_ERR_TIMEOUT"
+
+
 def test_table_bytes(lib):
     from paper_1908_05936_gb300 import _lib as L
     b = ctypes.c_int64()
