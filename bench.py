@@ -452,8 +452,11 @@ def time_ordered_mixed(t, torch, seed: int = 0) -> dict:
       against the plain insert / erase of the same draws;
     * a free-running mixed batch over the same draws (50 / 30 / 20 insert /
       find / erase, per position), against the three plain calls of its parts.
-    Every repetition starts from the same table contents: the draws' keys are
-    erased (untimed) after each timed call that inserts them."""
+    Every repetition starts from the same table: after each timed call that
+    inserts the draws' keys they are erased and the table is rehashed to its
+    own capacity (both untimed), so tombstones of earlier repetitions do not
+    lengthen the probes of later ones (the mixed batch's inserts claim EMPTY
+    slots only and would otherwise use up a few million per repetition)."""
     from paper_1908_05936_gb300.table import to_device
     from workloads import recipes, splitmix
     # 2^24 draws from 2^23 keys on the 2^28-slot table; fewer on smaller
@@ -486,14 +489,17 @@ def time_ordered_mixed(t, torch, seed: int = 0) -> dict:
 
     def reset():
         t.erase(d_keys, status=False)
+        t.rehash(cap)
         torch.cuda.synchronize()
 
     res = {k: [] for k in ("insert", "insert_ordered", "erase", "erase_ordered", "mixed", "parts")}
     for _ in range(4):
         res["insert"].append(timed(lambda: t.insert(d_keys, d_vals, status=st)))
         res["erase"].append(timed(lambda: t.erase(d_keys, status=st)))
+        t.rehash(cap)
         res["insert_ordered"].append(timed(lambda: t.insert_ordered(d_keys, d_vals, status=st, scratch=scratch)))
         res["erase_ordered"].append(timed(lambda: t.erase_ordered(d_keys, status=st, scratch=scratch)))
+        t.rehash(cap)
         res["mixed"].append(timed(lambda: t.apply_mixed(d_ops, d_keys, d_vals, status=st, vals_out=vo)))
         reset()
 

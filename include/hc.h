@@ -368,7 +368,8 @@ HC_API hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, 
  * hc_device_view fills *out for table t.  The view stays valid until the
  * table is rehashed or destroyed.  For maps the first call allocates the
  * lock bits (one per bucket, nb / 8 bytes rounded up to 4, zeroed on
- * `stream` and freed with the table) and synchronises `stream`. */
+ * `stream` and freed with the table) and synchronises `stream`; hc_rehash
+ * allocates new ones for the new bucket count when the table had them. */
 typedef struct hc_device_view {
     void *buckets;          /* device: nb buckets of bucket_bytes bytes          */
     void *header;           /* device: the table header (counters, side slots)   */

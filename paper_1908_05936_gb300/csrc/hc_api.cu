@@ -508,6 +508,8 @@ hc_rc hc_clear(hc_table *t, void *stream) {
     return HC_OK;
 }
 
+static hc_rc ensure_locks(hc_table *t, cudaStream_t s);
+
 hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
     hc_rc rc = check_table(t);
     if (rc != HC_OK) return rc;
@@ -546,7 +548,8 @@ hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
         return cuda_fail(e, "rehashing");
     }
     cudaFree(t->d_mem);
-    if (t->locks) {                       // sized for the old bucket count; the next view allocates anew
+    const bool had_locks = t->locks != nullptr;
+    if (had_locks) {                      // sized for the old bucket count
         cudaFree(t->locks);
         t->locks = nullptr;
     }
@@ -555,7 +558,9 @@ hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
     t->capacity = new_slots;
     t->phys = g.phys;
     t->bytes = g.bytes;
-    return HC_OK;
+    // a table that had lock bits gets its new ones here, not in the next
+    // in-kernel call (whose allocation would synchronise its stream)
+    return had_locks ? ensure_locks(t, s) : HC_OK;
 }
 
 static void fill_view(const hc_table *t, hc_device_view *out);

@@ -149,6 +149,40 @@ def test_in_kernel_overflow_and_no_tombstone_reuse(kind):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("bb", (32, 128))
+def test_in_kernel_inserts_reuse_slots_after_clear_and_rehash(kind, bb):
+    """In-kernel inserts claim EMPTY slots only; hc_clear makes every slot
+    EMPTY again and hc_rehash moves the keys to new slots (for maps with new
+    lock bits, allocated by the rehash).  Fill to a load factor of 0.85
+    in-kernel, erase some, clear, fill again with keys that overlap the first
+    set, rehash, fill on: every status, the contents and the size against
+    the oracle, and no retry bound is reached."""
+    rng = np.random.default_rng(700 + kind + bb)
+    reserved = {int(x) for x in C.bits(np.array(RESERVED[kind]))}
+    p = Pair(kind, 4096, bucket_bytes=bb)
+    try:
+        def fresh(n):
+            k = random_keys(kind, n, rng)
+            return k[[int(x) not in reserved for x in C.bits(k)]]
+        first = fresh(3480)
+        dev_insert(p, first)
+        dev_erase(p, first[:500])
+        p.check()
+        p.clear()
+        second = np.concatenate([first[1000:2500], fresh(1980)])
+        st, _ = dev_insert(p, second, salt=1)
+        assert (st != C.OVERFLOW).all()
+        p.check()
+        assert p.g.status() == L.OK
+        assert p.rehash(8192)
+        dev_insert(p, np.concatenate([second[:1000], fresh(2500)]), salt=2)
+        p.check()
+        assert p.g.status() == L.OK
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("bb", (32, 128))
 def test_free_running_mixed_ops(kind, bb):
     """Inserts, finds and erases of a small key domain from 2^18 threads in
     one launch (about 64 operations per key)."""
