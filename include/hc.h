@@ -259,21 +259,22 @@ HC_API hc_rc hc_unpack_short3(const int64_t *d_keys, int64_t n, int16_t *d_xyz, 
 
 /* ---- free-running mixed batches --------------------------------------------
  * One launch in which inserts, finds and erases of the same table run at
- * once, one operation per thread (Section 4, "Guarantees": concurrency across
- * all defined operations), with the in-kernel functions of
- * include/hc_device.cuh and their contract: for every key the results are
- * those of some serial order of that key's operations, no key is stored
- * twice, map values are seen only with their keys, inserts claim EMPTY slots
- * only (tombstones return with hc_clear / hc_rehash).  No order across keys
- * and no phase order is implied (the batched form's phases are the ordered
- * alternative).
+ * once (Section 4, "Guarantees": concurrency across all defined operations),
+ * under the contract of the in-kernel functions of include/hc_device.cuh:
+ * for every key the results are those of some serial order of that key's
+ * operations, no key is stored twice, map values are seen only with their
+ * keys, inserts claim EMPTY slots only (tombstones return with hc_clear /
+ * hc_rehash).  No order across keys and no phase order is implied (the
+ * batched form's phases are the ordered alternative).  The kernel stages
+ * each block's operations in shared memory and keeps several of them in
+ * flight per thread, as the range kernels do.
  *   d_ops[i]: 0 insert, 1 find, 2 erase (any other value erases).
  *   d_status[i] (may be NULL): insert / erase status, or 1 / 0 for a find
  *     that found / did not find its key.
- *   d_vals: map values of the inserts (read at insert positions only);
- *   d_vals_out (maps, may be NULL): values found (0 when absent).
- * For maps the first call allocates the table's lock bits (as
- * hc_device_view_get) and synchronises `stream`; otherwise asynchronous. */
+ *   d_vals: n map values, used at insert positions;
+ *   d_vals_out (maps, may be NULL): the value found at find positions, 0 at
+ *     every other position.
+ * Allocates nothing; asynchronous on `stream`. */
 HC_API hc_rc hc_apply_mixed(hc_table *t, const uint8_t *d_ops, const void *d_keys, const void *d_vals, int64_t n,
                             uint8_t *d_status, void *d_vals_out, void *stream);
 
@@ -353,10 +354,15 @@ HC_API hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, 
  *     kernels, may run concurrently on one table.  The results for one key
  *     are those of some serial order of that key's operations, and a key is
  *     never stored twice.
- *   - A map insert writes the value before its key becomes visible (under a
- *     lock bit of the bucket it claims in), so a find that sees a key reads
- *     the value stored with it.  Lookups take no lock (Section 4,
- *     "Concurrency": lookups are non-blocking).
+ *   - A map insert writes the value before its key becomes visible: it
+ *     claims an EMPTY slot by swapping in a marker (the key pattern all ones
+ *     minus two), stores the value, then the key, so a find that sees a key
+ *     reads the value stored with it.  No lock is taken; an insert that
+ *     meets a claim in progress where its own key could be going reads the
+ *     bucket again until the claim resolves.  Lookups and erases never wait
+ *     (Section 4, "Concurrency": lookups are non-blocking).  A key equal to
+ *     the marker is an ordinary key; the table header records where it is
+ *     stored.
  *   - In-kernel inserts claim EMPTY slots only, never tombstones: a
  *     tombstone reused concurrently with another insert of the same key could
  *     store the key twice.  Erased slots are reclaimed by hc_clear or
@@ -365,15 +371,12 @@ HC_API hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, 
  *   - Kernels that use the device functions and range calls on the same
  *     table must be ordered (one stream, or events), like any two calls.
  *
- * hc_device_view fills *out for table t.  The view stays valid until the
- * table is rehashed or destroyed.  For maps the first call allocates the
- * lock bits (one per bucket, nb / 8 bytes rounded up to 4, zeroed on
- * `stream` and freed with the table) and synchronises `stream`; hc_rehash
- * allocates new ones for the new bucket count when the table had them. */
+ * hc_device_view fills *out for table t; it allocates nothing and launches
+ * nothing (`stream` is unused).  The view stays valid until the table is
+ * rehashed or destroyed. */
 typedef struct hc_device_view {
     void *buckets;          /* device: nb buckets of bucket_bytes bytes          */
     void *header;           /* device: the table header (counters, side slots)   */
-    uint32_t *locks;        /* device: one lock bit per bucket (maps); NULL for sets */
     uint64_t nb;            /* number of buckets                                 */
     uint64_t seed;          /* hash seed                                         */
     int32_t kind;           /* hc_kind                                           */

@@ -20,6 +20,15 @@
 // so a table stores at most `capacity` keys in slots (fixed capacity,
 // Section 4).
 //
+// CLAIM (all ones minus two) is the key pattern an in-kernel map insert
+// (include/hc_device.cuh) writes into the EMPTY slot it claims before it
+// stores the value and then the key, so that a concurrent reader never sees
+// a key without its value.  A stored key with that bit pattern is an
+// ordinary key held in a slot; the header records its position (claim_key_at)
+// so that in-kernel map inserts tell it from a claim in progress.  Every
+// path that stores or erases it in a map keeps that record; range kernels run
+// between in-kernel ones and never see a claim in progress.
+//
 // Probing.  A key hashes to a first bucket; buckets are visited in order,
 // wrapping around, at most nb of them.  A group of G = KRB / LB lanes reads the
 // bucket's key region (KRB bytes) together, each lane LB bytes (16, 32, 64
@@ -65,10 +74,11 @@ struct alignas(256) Header {
     unsigned long long used;             // slots that are not EMPTY (keys + tombstones), padding excluded
     unsigned int err;                    // sticky ERR_* bits
     unsigned int side_present[2];        // [0]: all-ones key, [1]: all-ones-minus-one key
-    unsigned int side_lock;              // bits 0/1: side slot held by an in-kernel map insert
+    unsigned int side_lock;              // bits 0/1: side slot held by an in-kernel map insert; bit 2: CLAIM-key insert
     unsigned long long side_val[2];
     unsigned long long dump_count;       // output cursor of the dump kernel
     unsigned long long reinserted;       // counter of the rehash kernel
+    unsigned long long claim_key_at;     // maps: 1 + slot position of the stored key equal to CLAIM, 0 if none
 };
 static_assert(sizeof(Header) == 256, "header is one 256-byte block");
 
@@ -90,25 +100,25 @@ template <> struct Traits<KIND_SET_U32> {
     using Key = uint32_t;
     using Val = uint32_t;
     static constexpr bool MAP = false;
-    static constexpr Key EMPTY = 0xFFFFFFFFu, TOMB = 0xFFFFFFFEu;
+    static constexpr Key EMPTY = 0xFFFFFFFFu, TOMB = 0xFFFFFFFEu, CLAIM = 0xFFFFFFFDu;
 };
 template <> struct Traits<KIND_SET_U64> {
     using Key = unsigned long long;
     using Val = unsigned long long;
     static constexpr bool MAP = false;
-    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
+    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1, CLAIM = ~0ull - 2;
 };
 template <> struct Traits<KIND_MAP_I64_I32> {
     using Key = unsigned long long;   // int64 keys are handled as bit patterns
     using Val = uint32_t;             // int32 values likewise
     static constexpr bool MAP = true;
-    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
+    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1, CLAIM = ~0ull - 2;
 };
 template <> struct Traits<KIND_MAP_U64_U64> {
     using Key = unsigned long long;
     using Val = unsigned long long;
     static constexpr bool MAP = true;
-    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1;
+    static constexpr Key EMPTY = ~0ull, TOMB = ~0ull - 1, CLAIM = ~0ull - 2;
 };
 
 // ------------------------------------------------------------------ hash ---
@@ -384,6 +394,21 @@ __device__ __forceinline__ int side_index(typename Traits<KIND>::Key k) {
     return k == T::EMPTY ? 0 : (k == T::TOMB ? 1 : -1);
 }
 
+// The header's record of a stored key equal to CLAIM (maps): called when a
+// range or rehash kernel has stored key k at slot position pos, or erased it
+// (pos < 0).  No in-kernel insert runs meanwhile.
+template <int KIND>
+__device__ __forceinline__ void note_claim_key(Header *h, typename Traits<KIND>::Key k, long long pos) {
+    using T = Traits<KIND>;
+    if constexpr (T::MAP) {
+        if (k == T::CLAIM) h->claim_key_at = pos < 0 ? 0ull : (unsigned long long)pos + 1ull;
+    } else {
+        (void)h;
+        (void)k;
+        (void)pos;
+    }
+}
+
 // Per-key results of a tile before they are written.
 template <int KPT> struct TileResult {
     uint32_t st[KPT];
@@ -518,7 +543,10 @@ __device__ __forceinline__ void insert_group(const View &v, const typename Trait
             Key old = expect;
             if (grp.sub == owner) {
                 old = cas_key<KIND>(Slots<KIND, BB>::key(v, ffb[j], ffs_slot[j]), expect, k[j]);
-                if (old == expect) store_val<KIND, BB>(v, ffb[j], ffs_slot[j], val[j]);
+                if (old == expect) {
+                    store_val<KIND, BB>(v, ffb[j], ffs_slot[j], val[j]);
+                    note_claim_key<KIND>(v.hdr, k[j], (long long)(ffb[j] * Lay::SPB) + ffs_slot[j]);
+                }
             }
             old = grp.bcast(old, owner);
             if (old == expect) {
@@ -641,8 +669,10 @@ __device__ __forceinline__ void erase_group(const View &v, const typename Traits
             if (gm) {
                 const int owner = __ffs(gm) - 1;
                 Key old = T::TOMB;
-                if (grp.sub == owner)
+                if (grp.sub == owner) {
                     old = cas_key<KIND>(Slots<KIND, BB>::key(v, b[j], owner * SPL + (__ffs(lm) - 1)), k[j], T::TOMB);
+                    if (old == k[j]) note_claim_key<KIND>(v.hdr, k[j], -1);
+                }
                 old = grp.bcast(old, owner);
                 // a failed swap means an equal key in this batch erased it first
                 res.st[j] = old == k[j] ? ST_ERASED : ST_NOT_FOUND;

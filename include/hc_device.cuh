@@ -29,13 +29,16 @@
 //            are claimed, never tombstones.  Slots never become EMPTY again
 //            while kernels run, so every insert of one key reaches the same
 //            bucket and the same slot, and a key is stored at most once.
-//            Sets claim with one compare-and-swap of the key.  Maps take the
-//            bucket's lock bit first (one bit per bucket, an attempt that
-//            finds it held reads the bucket again: Section 5.2's locks
-//            without blocking), re-read the bucket, write the value, then
-//            the key, then release, so a reader that sees the key sees its
-//            value.  No EMPTY slot on the whole probe sequence: OVERFLOW.
-//   find     probes to the key or to a bucket holding EMPTY; takes no lock.
+//            Sets claim with one compare-and-swap of the key.  Maps claim
+//            the slot with a compare-and-swap to the CLAIM marker, store the
+//            value, fence, then store the key, so a reader that sees the key
+//            sees its value; no lock is taken.  An insert that meets a claim
+//            in progress where its own key could be going (before the first
+//            EMPTY slot of its scan order) reads the bucket again until the
+//            claim resolves.  No EMPTY slot on the whole probe sequence:
+//            OVERFLOW.
+//   find     probes to the key or to a bucket holding EMPTY; takes no lock
+//            and never waits (a claim in progress is not yet its key).
 //   erase    finds the key and swaps it for a tombstone.
 // Per key, the results of concurrent calls are those of some serial order
 // of them.  Counters (size) move with one atomic per group of threads that
@@ -69,7 +72,7 @@ namespace detail {
 using hc::Header;
 using hc::View;
 
-// Bounds every wait and retry (lock bit held, compare-and-swap lost); a
+// Bounds every wait and retry (claim in progress, side lock held, compare-and-swap lost); a
 // correct table never reaches it.
 constexpr uint32_t kMaxRetries = hc::kMaxRestarts;
 
@@ -93,18 +96,6 @@ __device__ __forceinline__ void count(Header *h, uint32_t ins, uint32_t del, uin
     }
 }
 
-__device__ __forceinline__ bool try_lock(uint32_t *words, unsigned long long i) {
-    const uint32_t bit = 1u << (i & 31);
-    if (atomicOr(&words[i >> 5], bit) & bit) return false;
-    __threadfence();                                  // acquire: the bucket is read after the bit is held
-    return true;
-}
-
-__device__ __forceinline__ void unlock(uint32_t *words, unsigned long long i) {
-    __threadfence();                                  // release: the slot's writes before the bit
-    atomicAnd(&words[i >> 5], ~(1u << (i & 31)));
-}
-
 // First set bit of `mask` at or after position `rot`, wrapping around.
 template <int SPB>
 __device__ __forceinline__ int first_from(uint32_t mask, int rot) {
@@ -113,20 +104,59 @@ __device__ __forceinline__ int first_from(uint32_t mask, int rot) {
     return __ffs(hi ? hi : mask) - 1;
 }
 
+// Slots that come before the first set bit of `empty` in the scan order that
+// starts at `rot` and wraps around (every slot when `empty` is 0).
+template <int SPB>
+__device__ __forceinline__ uint32_t before_first(uint32_t empty, int rot) {
+    constexpr uint32_t ALL = SPB >= 32 ? 0xFFFFFFFFu : ((1u << SPB) - 1u);
+    if (!empty) return ALL;
+    const int q = first_from<SPB>(empty, rot);
+    const uint32_t from_rot = ALL & ~((1u << rot) - 1u);
+    const uint32_t below_q = (1u << q) - 1u;
+    return q >= rot ? (from_rot & below_q) : (from_rot | below_q);
+}
+
 template <int KIND, int BB>
 __device__ __forceinline__ void scan(const View &v, unsigned long long b, typename hc::Traits<KIND>::Key k,
-                                     uint32_t &match, uint32_t &empty) {
+                                     uint32_t &match, uint32_t &empty, uint32_t &claim) {
     using S = hc::Slots<KIND, BB>;
     hc::LaneWords<S::KRB> lw;
     lw.load(hc::bucket_at<BB>(v, b));
     match = 0;
     empty = 0;
+    claim = 0;
 #pragma unroll
     for (int q = 0; q < S::SPB; ++q) {
         const auto ks = hc::slot_key<KIND, S::KRB>(lw, q);
         match |= (uint32_t)(ks == k) << q;
         empty |= (uint32_t)(ks == hc::Traits<KIND>::EMPTY) << q;
+        claim |= (uint32_t)(ks == hc::Traits<KIND>::CLAIM) << q;
     }
+}
+
+template <int KIND, int BB>
+__device__ __forceinline__ void scan(const View &v, unsigned long long b, typename hc::Traits<KIND>::Key k,
+                                     uint32_t &match, uint32_t &empty) {
+    uint32_t claim;
+    scan<KIND, BB>(v, b, k, match, empty, claim);
+}
+
+// Where the stored key equal to CLAIM is (1 + slot position), 0 if none.
+__device__ __forceinline__ unsigned long long claim_key_at(const View &v) {
+    return *((volatile unsigned long long *)&v.hdr->claim_key_at);
+}
+
+// Whether a map insert scanning bucket b from slot `rot` must read it again:
+// `claim` holds the slots showing the CLAIM pattern, `empty` the EMPTY ones.
+// The stored key equal to CLAIM is not a claim; a claim in progress before
+// the first EMPTY slot of the scan order could be an insert of the same key.
+// Out of line: claim patterns are rare, and the common path keeps its
+// registers.
+template <int SPB>
+__device__ __noinline__ bool must_wait(const View &v, unsigned long long b, uint32_t claim, uint32_t empty, int rot) {
+    const unsigned long long at = claim_key_at(v);
+    if (at && (at - 1) / SPB == b) claim &= ~(1u << (int)((at - 1) % SPB));
+    return (claim & before_first<SPB>(empty, rot)) != 0;
 }
 
 template <int KIND>
@@ -177,57 +207,120 @@ __device__ Inserted insert_side(const View &v, int side, unsigned long long val,
     return r;
 }
 
+// The key word of slot position pos (a regular slot), read from L2.
 template <int KIND, int BB>
-__device__ Inserted insert(const View &v, uint32_t *locks, typename hc::Traits<KIND>::Key k,
-                           unsigned long long val) {
+__device__ __forceinline__ typename hc::Traits<KIND>::Key slot_word(const View &v, unsigned long long pos) {
+    using S = hc::Slots<KIND, BB>;
+    const unsigned char *p = S::key(v, pos / S::SPB, (int)(pos % S::SPB));
+    return *reinterpret_cast<const volatile typename hc::Traits<KIND>::Key *>(p);
+}
+
+// Map insert of the key whose bit pattern equals CLAIM.  Such inserts take
+// turns on a header bit, so at most one of them probes at a time; under it
+// the header's record says whether the key is stored, and a new one is
+// stored in the first EMPTY slot of its scan order: claimed with the
+// pattern itself, the value stored, then the record set, which is what makes
+// it visible to in-kernel finds and erases.
+template <int KIND, int BB>
+__device__ __noinline__ Inserted insert_claim_key(const View &v, unsigned long long val) {
+    using T = hc::Traits<KIND>;
+    using S = hc::Slots<KIND, BB>;
+    constexpr int SPB = S::SPB;
+    constexpr uint32_t bit = 4u;
+    Header *h = v.hdr;
+    Inserted r{END, OVERFLOW};
+    uint32_t ins = 0, tries = 0;
+    bool bound = false;
+    while (atomicOr(&h->side_lock, bit) & bit) {
+        if (++tries > kMaxRetries) { bound = true; break; }
+    }
+    if (!bound) {
+        __threadfence();
+        const unsigned long long at = claim_key_at(v);
+        if (at && slot_word<KIND, BB>(v, at - 1) == T::CLAIM) {
+            r = Inserted{(long long)(at - 1), EXISTS};
+        } else {
+            const int rot = hc::slot_rotation<SPB>((unsigned long long)T::CLAIM);
+            unsigned long long b = hc::first_bucket(v, (unsigned long long)T::CLAIM);
+            for (unsigned long long p = 0; p < v.nb;) {
+                uint32_t lm, le;
+                scan<KIND, BB>(v, b, T::CLAIM, lm, le);
+                if (!le) {
+                    b = hc::next_bucket(v, b);
+                    ++p;
+                    continue;
+                }
+                const int q = first_from<SPB>(le, rot);
+                if (hc::cas_key<KIND>(S::key(v, b, q), T::EMPTY, T::CLAIM) != T::EMPTY) {
+                    if (++tries > kMaxRetries) { bound = true; break; }
+                    continue;                          // another key took it: read the bucket again
+                }
+                hc::store_val<KIND, BB>(v, b, q, val);
+                __threadfence();                       // the value before the record
+                const long long pos = (long long)(b * SPB) + q;
+                atomicExch(&h->claim_key_at, (unsigned long long)pos + 1ull);
+                r = Inserted{pos, INSERTED};
+                ins = 1;
+                break;
+            }
+        }
+        __threadfence();
+        atomicAnd(&h->side_lock, ~bit);
+    }
+    if (r.status == OVERFLOW) atomicOr(&h->err, bound ? (hc::ERR_PROBE_BOUND | hc::ERR_OVERFLOW) : hc::ERR_OVERFLOW);
+    count(h, ins, 0, ins);
+    return r;
+}
+
+template <int KIND, int BB>
+__device__ Inserted insert(const View &v, typename hc::Traits<KIND>::Key k, unsigned long long val) {
     using T = hc::Traits<KIND>;
     using S = hc::Slots<KIND, BB>;
     constexpr int SPB = S::SPB;
     const int side = hc::side_index<KIND>(k);
     if (side >= 0) return insert_side<KIND>(v, side, val, (long long)(v.nb * SPB) + side);
+    if constexpr (T::MAP) {
+        if (k == T::CLAIM) return insert_claim_key<KIND, BB>(v, val);
+    }
     const int rot = hc::slot_rotation<SPB>((unsigned long long)k);
     unsigned long long b = hc::first_bucket(v, (unsigned long long)k);
     Inserted r{END, OVERFLOW};
     uint32_t ins = 0, retries = 0;
     bool bound = false;
     for (unsigned long long p = 0; p < v.nb;) {
-        uint32_t lm, le;
-        scan<KIND, BB>(v, b, k, lm, le);
+        uint32_t lm, le, lc;
+        scan<KIND, BB>(v, b, k, lm, le, lc);
         if (lm) {
             r = Inserted{(long long)(b * SPB) + (__ffs(lm) - 1), EXISTS};
             break;
+        }
+        if constexpr (T::MAP) {
+            // CLAIM patterns: the stored key, or claims in progress; a claim
+            // where an insert of this key would also have gone: wait
+            if (lc && must_wait<SPB>(v, b, lc, le, rot)) {
+                if (++retries > kMaxRetries) { bound = true; break; }
+                __nanosleep(64);
+                continue;
+            }
         }
         if (!le) {
             b = hc::next_bucket(v, b);
             ++p;
             continue;
         }
+        const int q = first_from<SPB>(le, rot);
         if constexpr (T::MAP) {
-            if (!try_lock(locks, b)) {                 // held: read the bucket again
+            if (hc::cas_key<KIND>(S::key(v, b, q), T::EMPTY, T::CLAIM) != T::EMPTY) {
                 if (++retries > kMaxRetries) { bound = true; break; }
-                continue;
+                continue;                              // lost the slot: read the bucket again
             }
-            scan<KIND, BB>(v, b, k, lm, le);           // under the lock
-            if (lm || !le) {
-                unlock(locks, b);
-                if (lm) {
-                    r = Inserted{(long long)(b * SPB) + (__ffs(lm) - 1), EXISTS};
-                    break;
-                }
-                b = hc::next_bucket(v, b);
-                ++p;
-                continue;
-            }
-            const int q = first_from<SPB>(le, rot);
             hc::store_val<KIND, BB>(v, b, q, val);
             __threadfence();                           // the value before the key
             store_key<KIND>(S::key(v, b, q), k);
-            unlock(locks, b);
             r = Inserted{(long long)(b * SPB) + q, INSERTED};
             ins = 1;
             break;
         } else {
-            const int q = first_from<SPB>(le, rot);
             const auto old = hc::cas_key<KIND>(S::key(v, b, q), T::EMPTY, k);
             if (old == T::EMPTY) {
                 r = Inserted{(long long)(b * SPB) + q, INSERTED};
@@ -250,11 +343,18 @@ __device__ Inserted insert(const View &v, uint32_t *locks, typename hc::Traits<K
 
 template <int KIND, int BB>
 __device__ long long find(const View &v, typename hc::Traits<KIND>::Key k) {
+    using T = hc::Traits<KIND>;
     using S = hc::Slots<KIND, BB>;
     constexpr int SPB = S::SPB;
     const int side = hc::side_index<KIND>(k);
     if (side >= 0)
         return *((volatile unsigned int *)&v.hdr->side_present[side]) ? (long long)(v.nb * SPB) + side : END;
+    if constexpr (T::MAP) {
+        if (k == T::CLAIM) {                           // stored where the header's record says
+            const unsigned long long at = claim_key_at(v);
+            return (at && slot_word<KIND, BB>(v, at - 1) == T::CLAIM) ? (long long)(at - 1) : END;
+        }
+    }
     unsigned long long b = hc::first_bucket(v, (unsigned long long)k);
     for (unsigned long long p = 0; p < v.nb; ++p) {
         uint32_t lm, le;
@@ -282,6 +382,10 @@ __device__ uint32_t erase(const View &v, typename hc::Traits<KIND>::Key k) {
             const int q = (int)((unsigned long long)pos % SPB);
             // a failed swap means a concurrent erase of the same key won
             del = hc::cas_key<KIND>(S::key(v, b, q), k, T::TOMB) == k;
+            if constexpr (T::MAP) {
+                // the record goes unless a new insert of the key has set it
+                if (del && k == T::CLAIM) atomicCAS(&v.hdr->claim_key_at, (unsigned long long)pos + 1ull, 0ull);
+            }
         }
     }
     count(v.hdr, 0, del, 0);
@@ -321,7 +425,7 @@ public:
     using Val = typename hc::Traits<KIND>::Val;
     static constexpr bool is_map = hc::Traits<KIND>::MAP;
 
-    __host__ __device__ explicit Table(const hc_device_view &d) : locks_(d.locks), bb_(d.bucket_bytes) {
+    __host__ __device__ explicit Table(const hc_device_view &d) : bb_(d.bucket_bytes) {
         v_.buckets = static_cast<unsigned char *>(d.buckets);
         v_.hdr = static_cast<hc::Header *>(d.header);
         v_.nb = d.nb;
@@ -335,9 +439,9 @@ public:
     // Stores `key` (with `value` for maps) unless it is present.
     __device__ Inserted insert(Key key, Val value = Val()) const {
         switch (bb_) {
-            case 32: return detail::insert<KIND, 32>(v_, locks_, key, (unsigned long long)value);
-            case 64: return detail::insert<KIND, 64>(v_, locks_, key, (unsigned long long)value);
-            default: return detail::insert<KIND, 128>(v_, locks_, key, (unsigned long long)value);
+            case 32: return detail::insert<KIND, 32>(v_, key, (unsigned long long)value);
+            case 64: return detail::insert<KIND, 64>(v_, key, (unsigned long long)value);
+            default: return detail::insert<KIND, 128>(v_, key, (unsigned long long)value);
         }
     }
     // Position of `key`, or END.
@@ -423,7 +527,6 @@ private:
     }
 
     hc::View v_;
-    uint32_t *locks_;
     int bb_;
 };
 

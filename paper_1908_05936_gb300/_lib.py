@@ -81,7 +81,7 @@ class Predicate(ctypes.Structure):
 
 class DeviceView(ctypes.Structure):
     """hc_device_view: a table as the in-kernel functions see it."""
-    _fields_ = [("buckets", ctypes.c_void_p), ("header", ctypes.c_void_p), ("locks", ctypes.c_void_p),
+    _fields_ = [("buckets", ctypes.c_void_p), ("header", ctypes.c_void_p),
                 ("nb", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("kind", ctypes.c_int32),
                 ("bucket_bytes", ctypes.c_int32), ("hash_mode", ctypes.c_int32), ("pad_from", ctypes.c_int32)]
 

@@ -374,7 +374,6 @@ hc_rc hc_destroy(hc_table *t) {
     if (rc != HC_OK) return rc;
     t->magic = 0;
     cudaError_t e = cudaFree(t->d_mem);   // cudaFree waits for work queued on the device
-    if (t->locks) cudaFree(t->locks);
     if (t->stage_mem) {
         cudaFree(t->stage_mem);
         for (int i = 0; i < 2; ++i) {
@@ -508,8 +507,6 @@ hc_rc hc_clear(hc_table *t, void *stream) {
     return HC_OK;
 }
 
-static hc_rc ensure_locks(hc_table *t, cudaStream_t s);
-
 hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
     hc_rc rc = check_table(t);
     if (rc != HC_OK) return rc;
@@ -548,19 +545,12 @@ hc_rc hc_rehash(hc_table *t, int64_t new_slots, void *stream) {
         return cuda_fail(e, "rehashing");
     }
     cudaFree(t->d_mem);
-    const bool had_locks = t->locks != nullptr;
-    if (had_locks) {                      // sized for the old bucket count
-        cudaFree(t->locks);
-        t->locks = nullptr;
-    }
     t->d_mem = mem;
     t->view = nv;
     t->capacity = new_slots;
     t->phys = g.phys;
     t->bytes = g.bytes;
-    // a table that had lock bits gets its new ones here, not in the next
-    // in-kernel call (whose allocation would synchronise its stream)
-    return had_locks ? ensure_locks(t, s) : HC_OK;
+    return HC_OK;
 }
 
 static void fill_view(const hc_table *t, hc_device_view *out);
@@ -677,31 +667,9 @@ hc_rc hc_select(hc_table *t, const hc_predicate *pred, void *d_keys_out, void *d
     return HC_OK;
 }
 
-static hc_rc ensure_locks(hc_table *t, cudaStream_t s) {
-    if (is_map(t->kind) && !t->locks) {
-        const size_t words = (size_t)((t->view.nb + 31) / 32);
-        void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, words * sizeof(uint32_t));
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            return fail(HC_ERR_OOM, "cudaMalloc of %lld lock bytes failed: %s", (long long)(words * 4),
-                        cudaGetErrorString(e));
-        }
-        e = cudaMemsetAsync(p, 0, words * sizeof(uint32_t), s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            cudaFree(p);
-            return cuda_fail(e, "zeroing the lock bits");
-        }
-        t->locks = static_cast<uint32_t *>(p);
-    }
-    return HC_OK;
-}
-
 static void fill_view(const hc_table *t, hc_device_view *out) {
     out->buckets = t->view.buckets;
     out->header = t->view.hdr;
-    out->locks = t->locks;
     out->nb = t->view.nb;
     out->seed = t->view.seed;
     out->kind = t->kind;
@@ -742,7 +710,6 @@ hc_rc hc_device_view_get(hc_table *t, hc_device_view *out, void *stream) {
     hc_rc rc = check_table(t);
     if (rc != HC_OK) return rc;
     if (!out) return fail(HC_ERR_ARG, "out is NULL");
-    if ((rc = ensure_locks(t, static_cast<cudaStream_t>(stream))) != HC_OK) return rc;
     fill_view(t, out);
     return HC_OK;
 }
@@ -759,7 +726,6 @@ hc_rc hc_apply_mixed(hc_table *t, const uint8_t *d_ops, const void *d_keys, cons
     if (d_vals_out && is_map(t->kind) && (rc = check_array(d_vals_out, val_bytes(t->kind), "values output")) != HC_OK)
         return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((rc = ensure_locks(t, s)) != HC_OK) return rc;
     hc_device_view dv{};
     fill_view(t, &dv);
     const cudaError_t e = hc::mixed_ops(dv, d_ops, d_keys, is_map(t->kind) ? d_vals : nullptr, n, d_status,

@@ -138,6 +138,7 @@ k_rehash(View old_v, unsigned long long old_phys, View new_v) {
             }
             if (cas_key<KIND>(reinterpret_cast<unsigned char *>(bucket + s), T::EMPTY, key) == T::EMPTY) {
                 store_val<KIND, BB>(new_v, b, s, val);
+                note_claim_key<KIND>(new_v.hdr, key, (long long)(b * SPB) + s);
                 done = true;
             }
             // a lost race re-reads the same bucket

@@ -520,7 +520,10 @@ __device__ __forceinline__ void insert_stream_chunk(const View &v, const typenam
             if (!(claiming >> s & 1u)) continue;
             const Key expect = ff_empty[s] ? T::EMPTY : T::TOMB;
             if (old[s] == expect) {
-                if constexpr (T::MAP) store_val<KIND, BB>(v, ffb[s], ffs_slot[s], (unsigned long long)sv[idx[s]]);
+                if constexpr (T::MAP) {
+                    store_val<KIND, BB>(v, ffb[s], ffs_slot[s], (unsigned long long)sv[idx[s]]);
+                    note_claim_key<KIND>(v.hdr, key[s], (long long)(ffb[s] * SPL) + ffs_slot[s]);
+                }
                 ss[idx[s]] = ST_INSERTED;
                 ++cnt.ins;
                 cnt.new_slot += ff_empty[s] ? 1u : 0u;
@@ -661,6 +664,7 @@ __device__ __forceinline__ void erase_stream_chunk(const View &v, const typename
         for (int s = 0; s < S; ++s) {
             if (!(hitting >> s & 1u)) continue;
             const bool won = old[s] == key[s];
+            if (won) note_claim_key<KIND>(v.hdr, key[s], -1);
             ss[idx[s]] = won ? (uint8_t)ST_ERASED : (uint8_t)ST_NOT_FOUND;
             cnt.del += won ? 1u : 0u;
             finished |= 1u << s;

@@ -22,7 +22,6 @@ struct hc_table {
     hc::View view;
     hc::LaunchShape shape[3];
     bool shape_set[3] = {false, false, false};   // hc_set_launch was called for the op
-    uint32_t *locks = nullptr;   // lock bits of the in-kernel map insert (one per bucket), on first use
     // staging for the host-buffer calls (allocated on first use)
     void *stage_mem = nullptr;
     cudaStream_t copy_stream = nullptr;

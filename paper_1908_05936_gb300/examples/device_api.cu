@@ -22,9 +22,10 @@
 namespace {
 
 template <int KIND>
-__global__ void k_apply(hc_device_view dv, const uint8_t *ops, int op_all, const typename hcd::Table<KIND>::Key *keys,
-                        const typename hcd::Table<KIND>::Val *vals, long long n, uint8_t *status,
-                        typename hcd::Table<KIND>::Val *vals_out, long long *pos_out) {
+__device__ __forceinline__ void apply_one(hc_device_view dv, const uint8_t *ops, int op_all,
+                                          const typename hcd::Table<KIND>::Key *keys,
+                                          const typename hcd::Table<KIND>::Val *vals, long long n, uint8_t *status,
+                                          typename hcd::Table<KIND>::Val *vals_out, long long *pos_out) {
     using Tab = hcd::Table<KIND>;
     const Tab t(dv);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,6 +49,24 @@ __global__ void k_apply(hc_device_view dv, const uint8_t *ops, int op_all, const
     }
     if (status) status[i] = st;
     if (pos_out) pos_out[i] = pos;
+}
+
+// Sets keep the compiler's register count; maps are held to 40 registers per
+// thread, which their insert fits without spilling, for more threads (and
+// probes) in flight per SM.
+template <int KIND>
+__global__ void k_apply_set(hc_device_view dv, const uint8_t *ops, int op_all, const typename hcd::Table<KIND>::Key *keys,
+                            const typename hcd::Table<KIND>::Val *vals, long long n, uint8_t *status,
+                            typename hcd::Table<KIND>::Val *vals_out, long long *pos_out) {
+    apply_one<KIND>(dv, ops, op_all, keys, vals, n, status, vals_out, pos_out);
+}
+
+template <int KIND>
+__global__ void __maxnreg__(40) k_apply_map(hc_device_view dv, const uint8_t *ops, int op_all,
+                                            const typename hcd::Table<KIND>::Key *keys,
+                                            const typename hcd::Table<KIND>::Val *vals, long long n, uint8_t *status,
+                                            typename hcd::Table<KIND>::Val *vals_out, long long *pos_out) {
+    apply_one<KIND>(dv, ops, op_all, keys, vals, n, status, vals_out, pos_out);
 }
 
 // Block coordinates packed as three signed 21-bit fields (x | y << 21 | z << 42).
@@ -96,19 +115,19 @@ HCX_API hc_rc hcx_apply(const hc_device_view *dv, const uint8_t *ops, int32_t op
     long long *po = reinterpret_cast<long long *>(pos_out);
     switch (dv->kind) {
         case HC_SET_U32:
-            k_apply<HC_SET_U32><<<grid, block, 0, s>>>(*dv, ops, op_all, (const uint32_t *)keys, nullptr, n, status,
+            k_apply_set<HC_SET_U32><<<grid, block, 0, s>>>(*dv, ops, op_all, (const uint32_t *)keys, nullptr, n, status,
                                                        nullptr, po);
             break;
         case HC_SET_U64:
-            k_apply<HC_SET_U64><<<grid, block, 0, s>>>(*dv, ops, op_all, (const unsigned long long *)keys, nullptr, n,
+            k_apply_set<HC_SET_U64><<<grid, block, 0, s>>>(*dv, ops, op_all, (const unsigned long long *)keys, nullptr, n,
                                                        status, nullptr, po);
             break;
         case HC_MAP_I64_I32:
-            k_apply<HC_MAP_I64_I32><<<grid, block, 0, s>>>(*dv, ops, op_all, (const unsigned long long *)keys,
+            k_apply_map<HC_MAP_I64_I32><<<grid, block, 0, s>>>(*dv, ops, op_all, (const unsigned long long *)keys,
                                                            (const uint32_t *)vals, n, status, (uint32_t *)vals_out, po);
             break;
         case HC_MAP_U64_U64:
-            k_apply<HC_MAP_U64_U64><<<grid, block, 0, s>>>(*dv, ops, op_all, (const unsigned long long *)keys,
+            k_apply_map<HC_MAP_U64_U64><<<grid, block, 0, s>>>(*dv, ops, op_all, (const unsigned long long *)keys,
                                                            (const unsigned long long *)vals, n, status,
                                                            (unsigned long long *)vals_out, po);
             break;

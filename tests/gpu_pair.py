@@ -15,6 +15,22 @@ RESERVED = {
     O.MAP_U64_U64: (np.uint64(2**64 - 1), np.uint64(2**64 - 2)),
 }
 
+# The pattern an in-kernel map insert writes into the slot it claims, before
+# the value and the key (all ones minus two).  It is an ordinary key: held in
+# a slot, counted against the capacity, and found where the table header
+# records it; the test domains carry it so that every path meets it.
+CLAIM_PATTERN = {
+    O.SET_U32: np.uint32(0xFFFFFFFD),
+    O.SET_U64: np.uint64(2**64 - 3),
+    O.MAP_I64_I32: np.int64(-3),
+    O.MAP_U64_U64: np.uint64(2**64 - 3),
+}
+
+
+def edge_keys(kind: int) -> np.ndarray:
+    """The two side-slot patterns and the claim pattern of `kind`."""
+    return np.array(list(RESERVED[kind]) + [CLAIM_PATTERN[kind]], dtype=O.KEY_DTYPE[kind])
+
 
 def random_keys(kind: int, n: int, rng: np.random.Generator, domain: np.ndarray | None = None) -> np.ndarray:
     kdt = O.KEY_DTYPE[kind]

@@ -18,7 +18,7 @@ import torch
 
 import compare as C
 import linearizable as LZ
-from gpu_pair import RESERVED, Pair, random_keys, value_for
+from gpu_pair import CLAIM_PATTERN, RESERVED, Pair, edge_keys, random_keys, value_for
 from oracle import oracle as O
 from paper_1908_05936_gb300 import _lib as L
 from paper_1908_05936_gb300 import device_api as D
@@ -76,7 +76,7 @@ def _positions_consistent(keys, pos, ok):
 def test_in_kernel_ops_match_oracle(kind, bb):
     rng = np.random.default_rng(500 + kind * 7 + bb)
     p = Pair(kind, 60000, bucket_bytes=bb)
-    dom = np.concatenate([random_keys(kind, 12000, rng), np.array(RESERVED[kind])])
+    dom = np.concatenate([random_keys(kind, 12000, rng), edge_keys(kind)])
     try:
         for b, n in enumerate((0, 1, 100, 5000, 12000)):
             keys = dom[rng.integers(0, len(dom), size=n)]
@@ -188,7 +188,7 @@ def test_free_running_mixed_ops(kind, bb):
     one launch (about 64 operations per key)."""
     rng = np.random.default_rng(700 + kind * 3 + bb)
     t = Table(kind, 1 << 19, bucket_bytes=bb)
-    dom = np.concatenate([random_keys(kind, 1 << 12, rng), np.array(RESERVED[kind])])
+    dom = np.concatenate([random_keys(kind, 1 << 12, rng), edge_keys(kind)])
     dom = dom[np.unique(C.bits(dom), return_index=True)[1]]
     try:
         pre = dom[rng.random(len(dom)) < 0.5]
@@ -223,12 +223,13 @@ def test_free_running_mixed_ops(kind, bb):
 
 
 @pytest.mark.parametrize("kind", KINDS)
-def test_apply_mixed_serial_order_per_key(kind):
+@pytest.mark.parametrize("bb", (32, 64, 128))
+def test_apply_mixed_serial_order_per_key(kind, bb):
     """hc_apply_mixed (the library's free-running mixed batch) under the same
     per-key check, with 2^20 operations over 2^14 keys."""
-    rng = np.random.default_rng(750 + kind)
-    t = Table(kind, 1 << 21, bucket_bytes=64)
-    dom = random_keys(kind, 1 << 14, rng)
+    rng = np.random.default_rng(750 + kind + bb)
+    t = Table(kind, 1 << 21, bucket_bytes=bb)
+    dom = np.concatenate([random_keys(kind, 1 << 14, rng), edge_keys(kind)])
     dom = dom[np.unique(C.bits(dom), return_index=True)[1]]
     try:
         before = set()
@@ -246,12 +247,60 @@ def test_apply_mixed_serial_order_per_key(kind):
             after = {int(x) for x in kb}
             assert LZ.check_history(C.bits(keys), ops, st, before, after) == []
             if t.is_map:
+                got = to_numpy(vo, O.VAL_DTYPE[kind])
                 found = (ops == 1) & (st == 1)
-                assert np.array_equal(C.bits(to_numpy(vo, O.VAL_DTYPE[kind])[found]), C.bits(vals[found]))
+                assert np.array_equal(C.bits(got[found]), C.bits(vals[found]))
+                assert not C.bits(got[~found]).any(), "a value out where no key was found"
+                assert np.array_equal(C.bits(gv), C.bits(value_for(kind, gk)))
             assert t.status() == L.OK
             before = after
     finally:
         t.close()
+
+
+@pytest.mark.parametrize("kind", [O.MAP_I64_I32, O.MAP_U64_U64])
+@pytest.mark.parametrize("how", ["range", "in-kernel"])
+def test_in_kernel_map_inserts_past_a_stored_claim_pattern_key(kind, how):
+    """A map insert in a kernel waits only for claims in progress, never for
+    the stored key whose bit pattern equals the claim marker.  That key is put
+    into a 64-slot table (by a range call or in-kernel), most of the table is
+    filled around it in-kernel, so that nearly every later probe crosses its
+    bucket, then it is erased and inserted again while other keys go in: every
+    status, value and the contents against the oracle, and no retry bound
+    reached (a wait on the stored key would end at that bound).  In-kernel
+    inserts do not reuse tombstones, so the script stays below the capacity
+    (at most 59 of 64 slots used before the rehash)."""
+    rng = np.random.default_rng(900 + kind)
+    claim = np.array([CLAIM_PATTERN[kind]])
+    p = Pair(kind, 64, bucket_bytes=32)
+    try:
+        if how == "range":
+            p.insert(claim, value_for(kind, claim))
+        else:
+            dev_insert(p, claim)
+        for rep in range(3):
+            keys = np.concatenate([random_keys(kind, 15, rng), claim])
+            dev_insert(p, keys, salt=rep)
+            p.check()
+            assert p.g.status() == L.OK
+            dev_find(p, np.concatenate([keys, claim]))
+        dev_erase(p, claim)
+        p.check()
+        keys = np.concatenate([claim, random_keys(kind, 6, rng), claim])
+        dev_insert(p, keys, salt=7)
+        p.check()
+        p.erase(claim)
+        dev_find(p, claim)
+        p.insert(claim, value_for(kind, claim, salt=8))
+        dev_insert(p, np.concatenate([claim, random_keys(kind, 4, rng)]), salt=9)
+        p.check()
+        assert p.rehash(64)
+        dev_find(p, claim)
+        dev_erase(p, claim)
+        p.check()
+        assert p.g.status() == L.OK
+    finally:
+        p.close()
 
 
 def _pack21(x, y, z):

@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import compare as C
-from gpu_pair import RESERVED, Pair, random_keys
+from gpu_pair import RESERVED, Pair, edge_keys, random_keys
 from oracle import oracle as O
 from paper_1908_05936_gb300 import _lib as L
 from paper_1908_05936_gb300.table import Table, to_device, to_numpy
@@ -32,7 +32,7 @@ def _values(kind, n, rng):
 def test_ordered_equals_sequential(kind, bb):
     rng = np.random.default_rng(1100 + kind * 3 + bb)
     p = Pair(kind, 40000, bucket_bytes=bb)
-    dom = np.concatenate([random_keys(kind, 3000, rng), np.array(RESERVED[kind])])
+    dom = np.concatenate([random_keys(kind, 3000, rng), edge_keys(kind)])
     try:
         for n in (0, 1, 2, 255, 256, 257, 10000, 20000):
             keys = dom[rng.integers(0, len(dom), size=n)]

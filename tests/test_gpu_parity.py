@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import compare as C
-from gpu_pair import RESERVED, Pair, random_keys, value_for
+from gpu_pair import RESERVED, Pair, edge_keys, random_keys, value_for
 from paper_1908_05936_gb300.table import to_device, to_numpy
 from oracle import oracle as O
 
@@ -35,7 +35,7 @@ def built():
 def run_script(kind, slots, shape, seed, n_batches=30, domain_size=3000, max_batch=5000, rehash=True):
     bb, lb, kpt, block, fold = shape
     rng = np.random.default_rng(seed)
-    dom = np.concatenate([random_keys(kind, domain_size, rng), np.array(RESERVED[kind])])
+    dom = np.concatenate([random_keys(kind, domain_size, rng), edge_keys(kind)])
     p = Pair(kind, slots, bucket_bytes=bb, seed=seed,
              shape=dict(lane_bytes=lb, keys_per_group=kpt, block=block, fold=fold))
     try:
@@ -314,7 +314,7 @@ def test_streaming_insert(kind, bb, kpt):
     p = Pair(kind, 6000, bucket_bytes=bb)
     krb = p.g.get_launch(0)["lane_bytes"]
     p.g.set_launch(0, lane_bytes=krb, keys_per_group=kpt, block=64)
-    dom = np.concatenate([random_keys(kind, 5000, rng), np.array(RESERVED[kind])])
+    dom = np.concatenate([random_keys(kind, 5000, rng), edge_keys(kind)])
     try:
         for b, n in enumerate((0, 1, 63, 64, 65, 64 * kpt + 3, 3000, 3000)):
             keys = dom[rng.integers(0, len(dom), size=n)]
@@ -359,7 +359,7 @@ def test_streaming_erase(kind, bb, kpt):
     krb = p.g.get_launch(0)["lane_bytes"]
     for op in (0, 1, 2):
         p.g.set_launch(op, lane_bytes=krb, keys_per_group=kpt, block=128)
-    dom = np.concatenate([random_keys(kind, 7000, rng), np.array(RESERVED[kind])])
+    dom = np.concatenate([random_keys(kind, 7000, rng), edge_keys(kind)])
     try:
         p.insert(dom[:6000], value_for(kind, dom[:6000]))
         for b, n in enumerate((0, 1, 127, 128, 129, 128 * kpt + 5, 2500, 5000)):
