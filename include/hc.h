@@ -494,7 +494,10 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
  *      arrival order), while they fit (at most max_items); with merge = 1 it
  *      takes either small requests (up to 65536 keys), run as one
  *      hc_batch_run (or as the range call of a lone one), or one large
- *      request, run as its range call; with merge = 0 one request.  It
+ *      request, run as its range call; with merge = 0 one request.  Merged
+ *      mode merges only what the lane's free slots cannot take one by one:
+ *      with w heads waiting and f free slots, a slot takes w - f + 1 of them
+ *      and each other free slot one.  It
  *      copies the inputs host->device (small requests packed into one copy),
  *      launches, copies the results device->host and records an event;
  *   4. a finished slot hands each request its results and completion time.

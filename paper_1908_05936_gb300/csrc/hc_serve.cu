@@ -434,15 +434,17 @@ hc_rc serve_loop(hc_server *srv, const Source &src, double timeout_s, hc_serve_s
             int mode = 0;                     // 1: small units merged, 2: one large unit
             size_t skipped = nt_none;         // first large head passed over by a merged launch
             const size_t nt = tabs.size();
-            // merged mode merges only when more units wait than the lane has
-            // free slots; otherwise each takes a slot of its own, as in plain
-            // mode, and nothing waits for a batched launch
+            // merged mode merges only the units that the lane's free slots
+            // cannot take one by one: with w units waiting and f free slots
+            // (this one included), this slot takes w - f + 1 of them and each
+            // other free slot one, so nothing waits for a batched launch that
+            // a slot of its own could have run as its plain call
             int take = srv->max_items;
             if (srv->merge) {
                 int free_slots = 0, waiting = 0;
                 for (const Slot &o : srv->slots) free_slots += (o.lane == sl.lane && !o.busy) ? 1 : 0;
                 for (int t : tabs) waiting += (!fifo[(size_t)t].empty() && !inflight[(size_t)t]) ? 1 : 0;
-                if (waiting <= free_slots) take = 1;
+                take = waiting <= free_slots ? 1 : std::min(srv->max_items, waiting - free_slots + 1);
             }
             for (size_t j = 0; j < nt && (int)batch.size() < take && mode != 2; ++j) {
                 const int t = tabs[(rr[(size_t)sl.lane] + j) % nt];
