@@ -1006,7 +1006,10 @@ def run_served(args):
     First each form serves every request as fast as it can (its capacity:
     the median of three passes after an untimed one); then both serve
     real-time arrivals at 50 %, 80 % and 100 % of the plain path's capacity,
-    nine runs each (medians over the runs reported)."""
+    fifteen runs each (medians over the runs reported: a third or more of the
+    runs of either form can show a pause of tens of ms of the loop's host
+    thread on the shared host, and a median over nine runs was sometimes such
+    a run)."""
     import torch
     from paper_1908_05936_gb300 import _lib as L
     from paper_1908_05936_gb300 import build
@@ -1057,7 +1060,7 @@ def run_served(args):
     cap = capacity(plain)
     cap_rate = cap["requests"] / cap["wall_s"]
     cap_merged = capacity(merged)
-    # each load point nine times per form, alternating; p50, p99 and Mops/s
+    # each load point fifteen times per form, alternating; p50, p99 and Mops/s
     # are the medians over the runs (a p99 of 3000 requests rests on 30 of
     # them, and the loop's single host thread shares the host: a run whose
     # thread is held off the CPU for tens of ms shows it in every figure)
@@ -1069,7 +1072,7 @@ def run_served(args):
     for frac in (0.5, 0.8, 1.0):
         rate = frac * cap_rate
         runs = {"plain": [], "merged": []}
-        for _ in range(9):
+        for _ in range(15):
             runs["plain"].append(plain.run(requests(rate), realtime=True))
             runs["merged"].append(merged.run(requests(rate), realtime=True))
         loads[f"{int(frac * 100)}%"] = {"rate_req_per_s": round(rate, 1), "plain": median_run(runs["plain"]),
@@ -1131,7 +1134,7 @@ def _pick_served(r):
                                          "p99_runs": v[form]["p99_runs"]}
                                   for form in ("plain", "merged")} | {"rate_req_per_s": v["rate_req_per_s"]}
                            for load, v in r["loads"].items()},
-            "note": "medians over nine runs per load point and form; p99_runs lists every run",
+            "note": "medians over fifteen runs per load point and form; p99_runs lists every run",
             "clocks": r["clocks"]}
 
 
