@@ -40,7 +40,7 @@ BYTES_PER_OP = {"insert": 16 + 1 + 32 + 32, "find": 8 + 8 + 1 + 32, "erase": 8 +
 # they inserted; `requests_per_op` the same for lts__t_requests_srcunit_tex.sum
 # (requests from the SMs to L2).  Valid only while the kernel sources hash to
 # `digest`.
-INSERT_TRAFFIC = {"bytes_per_op": 227.7, "requests_per_op": 3.545, "digest": "e8348ec45d461564"}
+INSERT_TRAFFIC = {"bytes_per_op": 227.7, "requests_per_op": 3.545, "digest": "a09fabcd81947d1e"}
 
 
 def insert_kernel_digest() -> str:
