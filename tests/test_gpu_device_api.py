@@ -258,6 +258,53 @@ def test_apply_mixed_serial_order_per_key(kind, bb):
         t.close()
 
 
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("bb", (32, 128))
+def test_apply_mixed_on_a_table_that_fills_up(kind, bb):
+    """hc_apply_mixed on a 96-slot table: 2^14 mixed operations (60 / 20 / 20
+    insert / find / erase) over 400 keys plus the edge patterns, so the
+    table runs out of EMPTY slots during the launch (inserts do not reuse
+    tombstones).  Every insert reports INSERTED, EXISTS or OVERFLOW; per key
+    the results admit a serial order in which an OVERFLOW insert found the
+    key absent; no key is stored twice; at most the capacity is stored in
+    slots; found values are the inserted ones."""
+    rng = np.random.default_rng(820 + kind + bb)
+    cap = 96
+    t = Table(kind, cap, bucket_bytes=bb)
+    dom = np.concatenate([random_keys(kind, 400, rng), edge_keys(kind)])
+    dom = dom[np.unique(C.bits(dom), return_index=True)[1]]
+    side = {int(x) for x in C.bits(np.array(RESERVED[kind]))}
+    try:
+        pre = dom[rng.random(len(dom)) < 0.1]
+        pv = value_for(kind, pre)
+        t.insert(to_device(pre), to_device(pv) if pv is not None else None)
+        before = {int(x) for x in C.bits(t.dump_numpy()[0])}
+        for rep in range(2):
+            n = 1 << 14
+            keys = dom[rng.integers(0, len(dom), size=n)]
+            ops = rng.choice(np.array([0, 1, 2], dtype=np.uint8), size=n, p=[0.6, 0.2, 0.2])
+            vals = value_for(kind, keys)
+            st, vo = t.apply_mixed(to_device(ops), to_device(keys), to_device(vals) if vals is not None else None,
+                                   vals_out=t.is_map)
+            st = to_numpy(st, np.uint8)
+            gk, gv = t.dump_numpy()
+            kb = C.bits(gk)
+            assert len(np.unique(kb)) == len(kb) == t.size(), "a key stored twice, or size off"
+            assert sum(1 for x in kb.tolist() if int(x) not in side) <= cap
+            after = {int(x) for x in kb}
+            assert LZ.check_history(C.bits(keys), ops, st, before, after, overflow=True) == []
+            if t.is_map:
+                got = to_numpy(vo, O.VAL_DTYPE[kind])
+                found = (ops == 1) & (st == 1)
+                assert np.array_equal(C.bits(got[found]), C.bits(vals[found]))
+                assert np.array_equal(C.bits(gv), C.bits(value_for(kind, gk)))
+            assert t.status() in (L.OK, L.ERR_OVERFLOW)
+            before = after
+        assert (st == C.OVERFLOW).any(), "the table never filled up"
+    finally:
+        t.close()
+
+
 @pytest.mark.parametrize("kind", [O.MAP_I64_I32, O.MAP_U64_U64])
 @pytest.mark.parametrize("how", ["range", "in-kernel"])
 def test_in_kernel_map_inserts_past_a_stored_claim_pattern_key(kind, how):

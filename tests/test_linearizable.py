@@ -7,9 +7,9 @@ import numpy as np
 import linearizable as LZ
 
 
-def _random_result(op, rng):
+def _random_result(op, rng, overflow=False):
     if op == LZ.OP_INSERT:
-        return rng.choice([LZ.INSERTED, LZ.EXISTS])
+        return rng.choice([LZ.INSERTED, LZ.EXISTS, LZ.OVERFLOW] if overflow else [LZ.INSERTED, LZ.EXISTS])
     if op == LZ.OP_ERASE:
         return rng.choice([LZ.ERASED, LZ.NOT_FOUND])
     return rng.choice([0, 1])
@@ -29,6 +29,27 @@ def test_counting_rule_equals_brute_force():
         assert LZ.key_ok(before, after, ops) == want, (before, after, ops)
         agree[want] += 1
     assert agree[True] > 200 and agree[False] > 200     # both outcomes exercised
+
+
+def test_counting_rule_with_overflow_equals_brute_force():
+    """Histories of a table that fills up: an insert may report OVERFLOW
+    (observed the key absent, changed nothing)."""
+    rng = random.Random(9)
+    agree = {True: 0, False: 0}
+    for _ in range(4000):
+        ops = []
+        for _ in range(rng.randint(0, 6)):
+            o = rng.choice([LZ.OP_INSERT, LZ.OP_FIND, LZ.OP_ERASE])
+            ops.append((o, _random_result(o, rng, overflow=True)))
+        before, after = rng.randint(0, 1), rng.randint(0, 1)
+        want = LZ.serial_order_exists(before, after, ops, overflow=True)
+        assert LZ.key_ok(before, after, ops, overflow=True) == want, (before, after, ops)
+        agree[want] += 1
+    assert agree[True] > 200 and agree[False] > 200
+    I = LZ.OP_INSERT
+    assert LZ.key_ok(0, 0, [(I, LZ.OVERFLOW)], overflow=True)
+    assert not LZ.key_ok(1, 1, [(I, LZ.OVERFLOW)], overflow=True)      # present: EXISTS, not OVERFLOW
+    assert LZ.key_ok(0, 1, [(I, LZ.OVERFLOW), (I, LZ.INSERTED)], overflow=True)
 
 
 def test_serial_runs_pass_and_single_flips_are_judged_like_brute_force():
