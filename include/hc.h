@@ -497,14 +497,19 @@ HC_API hc_rc hc_batch_run_noalloc(const hc_batch_item *items, int64_t n_items, c
  *      request, run as its range call; with merge = 0 one request.  Merged
  *      mode merges only what the lane's free slots cannot take one by one:
  *      with w heads waiting and f free slots, a slot takes w - f + 1 of them
- *      and each other free slot one.  It
- *      copies the inputs host->device (small requests packed into one copy),
- *      launches, copies the results device->host and records an event;
+ *      and each other free slot one.  A request whose arrays are all
+ *      page-locked (keys, values of a map insert, status, values out of a
+ *      map find) runs where it is: the kernels read and write those arrays
+ *      through their mapped addresses (over NVLink-C2C), with no copy and
+ *      no room taken in the slot.  For the others the slot copies the inputs
+ *      host->device (small requests packed into one copy) and the results
+ *      back.  It launches and records an event;
  *   4. a finished slot hands each request its results and completion time.
- * A request larger than a slot is cut into chunks that fit, run one after
- * another before the table's next request; each chunk is one concurrent
- * batch of the request's operation.  Requests wait for a slot; a request is
- * dropped only when its deadline passes before any of it was dispatched.
+ * A request larger than a slot that does not run in place is cut into
+ * chunks that fit, run one after another before the table's next request;
+ * each chunk is one concurrent batch of the request's operation.  Requests
+ * wait for a slot; a request is dropped only when its deadline passes before
+ * any of it was dispatched.
  *
  * Two ways to feed the loop:
  *   - hc_server_run: a list of requests with arrival times, served on the

@@ -65,6 +65,7 @@ struct Placed {
     int64_t o_off, vo_off;         // device offsets of the outputs (vo_off < 0: none)
     bool packed;                   // inputs copied through the slot's host staging
     bool direct_out;               // outputs copied straight into the request's page-locked arrays
+    bool in_place;                 // all arrays page-locked: the kernels use them where they are
 };
 
 bool page_locked(const void *p) {
@@ -75,6 +76,17 @@ bool page_locked(const void *p) {
         return false;
     }
     return a.type == cudaMemoryTypeHost;
+}
+
+// The device address of a page-locked host array, or nullptr.
+unsigned char *mapped_addr(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<unsigned char *>(a.devicePointer) : nullptr;
 }
 
 struct Slot {
@@ -99,7 +111,14 @@ struct Track {
     int64_t units_left;            // units not yet completed
     int64_t dispatched;            // units handed to a slot
     bool out_locked;               // outputs page-locked (large units copy into them directly)
+    bool in_place = false;         // every array page-locked: no staging, no copies
+    unsigned char *dk = nullptr, *dv = nullptr, *ds = nullptr, *dvo = nullptr;   // their device addresses
 };
+
+// Whether request r can run where its arrays are: keys, values (map
+// inserts), status (when given) and values out (map finds, when given) all
+// page-locked.  Fills the device addresses.
+bool map_in_place(const hc_server *s, Track &t);
 
 }  // namespace
 
@@ -175,6 +194,19 @@ bool outputs_locked(const hc_server *s, const hc_request &r) {
     return (!r.h_status || page_locked(r.h_status)) && (!vals || page_locked(r.h_vals_out));
 }
 
+bool map_in_place(const hc_server *s, Track &t) {
+    const hc_request &r = *t.r;
+    if (r.n == 0) return false;
+    const bool map = val_bytes(s->tables[r.table]->kind) != 0;
+    t.dk = mapped_addr(r.h_keys);
+    if (!t.dk) return false;
+    if (r.op == HC_OP_INSERT && map && !(t.dv = mapped_addr(r.h_vals))) return false;
+    if (r.h_status && !(t.ds = mapped_addr(r.h_status))) return false;
+    if (r.op == HC_OP_FIND && !t.ds) return false;                 // a find needs its flags array
+    if (r.op == HC_OP_FIND && map && r.h_vals_out && !(t.dvo = mapped_addr(r.h_vals_out))) return false;
+    return true;
+}
+
 hc_rc launch(hc_server *s, Slot &sl, std::vector<Track> &tr, const std::vector<Unit> &batch) {
     cudaStream_t st = sl.stream;
     sl.placed.clear();
@@ -183,10 +215,14 @@ hc_rc launch(hc_server *s, Slot &sl, std::vector<Track> &tr, const std::vector<U
         const hc_request &r = *tr[(size_t)u.req].r;
         const int kind = s->tables[r.table]->kind;
         const int kb = key_bytes(kind), vb = val_bytes(kind);
+        if (tr[(size_t)u.req].in_place) {          // no staging: the kernels use the request's arrays
+            sl.placed.push_back(Placed{u, -1, -1, -1, -1, false, false, true});
+            continue;
+        }
         int64_t in, out;
         need(s, r, u.n, &in, &out);
         Placed p{u, off, (r.op == HC_OP_INSERT && vb) ? off + round256(u.n * kb) : -1, 0, -1, u.n <= kPackLimit,
-                 u.n > kPackLimit && tr[(size_t)u.req].out_locked};
+                 u.n > kPackLimit && tr[(size_t)u.req].out_locked, false};
         if (p.packed && u.n > 0) {
             std::memcpy(sl.h_in + p.k_off, static_cast<const unsigned char *>(r.h_keys) + u.off * kb,
                         (size_t)(u.n * kb));
@@ -205,7 +241,7 @@ hc_rc launch(hc_server *s, Slot &sl, std::vector<Track> &tr, const std::vector<U
     sl.out_begin = o;
     for (int pass = 0; pass < 2; ++pass) {
         for (Placed &p : sl.placed) {
-            if (p.direct_out != (pass == 1)) continue;
+            if (p.in_place || p.direct_out != (pass == 1)) continue;
             const hc_request &r = *tr[(size_t)p.u.req].r;
             const int vb = val_bytes(s->tables[r.table]->kind);
             p.o_off = o;
@@ -219,7 +255,7 @@ hc_rc launch(hc_server *s, Slot &sl, std::vector<Track> &tr, const std::vector<U
     cudaError_t e = cudaSuccess;
     if (packed_end > 0) e = cudaMemcpyAsync(sl.d_buf, sl.h_in, (size_t)packed_end, cudaMemcpyHostToDevice, st);
     for (const Placed &p : sl.placed) {
-        if (p.packed || p.u.n == 0 || e != cudaSuccess) continue;
+        if (p.in_place || p.packed || p.u.n == 0 || e != cudaSuccess) continue;
         const hc_request &r = *tr[(size_t)p.u.req].r;
         const int kind = s->tables[r.table]->kind;
         const int kb = key_bytes(kind), vb = val_bytes(kind);
@@ -232,15 +268,25 @@ hc_rc launch(hc_server *s, Slot &sl, std::vector<Track> &tr, const std::vector<U
     if (e != cudaSuccess) return scuda(e, "copying request inputs to the device");
     sl.items.clear();
     for (const Placed &p : sl.placed) {
-        const hc_request &r = *tr[(size_t)p.u.req].r;
+        const Track &t = tr[(size_t)p.u.req];
+        const hc_request &r = *t.r;
         hc_batch_item it{};
         it.table = s->tables[r.table];
         it.op = r.op;
-        it.d_keys = sl.d_buf + p.k_off;
-        it.d_vals = p.v_off >= 0 ? sl.d_buf + p.v_off : nullptr;
         it.n = p.u.n;
-        it.d_out = sl.d_buf + p.o_off;
-        it.d_vals_out = p.vo_off >= 0 ? sl.d_buf + p.vo_off : nullptr;
+        if (p.in_place) {
+            const int kind = s->tables[r.table]->kind;
+            const int kb = key_bytes(kind), vb = val_bytes(kind);
+            it.d_keys = t.dk + p.u.off * kb;
+            it.d_vals = t.dv ? t.dv + p.u.off * vb : nullptr;
+            it.d_out = t.ds ? t.ds + p.u.off : nullptr;
+            it.d_vals_out = t.dvo ? t.dvo + p.u.off * vb : nullptr;
+        } else {
+            it.d_keys = sl.d_buf + p.k_off;
+            it.d_vals = p.v_off >= 0 ? sl.d_buf + p.v_off : nullptr;
+            it.d_out = sl.d_buf + p.o_off;
+            it.d_vals_out = p.vo_off >= 0 ? sl.d_buf + p.vo_off : nullptr;
+        }
         sl.items.push_back(it);
     }
     hc_rc rc = HC_OK;
@@ -262,7 +308,7 @@ hc_rc launch(hc_server *s, Slot &sl, std::vector<Track> &tr, const std::vector<U
         e = cudaMemcpyAsync(sl.h_out + sl.out_begin, sl.d_buf + sl.out_begin, (size_t)(sl.out_end - sl.out_begin),
                             cudaMemcpyDeviceToHost, st);
     for (const Placed &p : sl.placed) {
-        if (!p.direct_out || e != cudaSuccess) continue;
+        if (p.in_place || !p.direct_out || e != cudaSuccess) continue;
         const hc_request &r = *tr[(size_t)p.u.req].r;
         const int vb = val_bytes(s->tables[r.table]->kind);
         if (r.h_status) e = cudaMemcpyAsync(r.h_status + p.u.off, sl.d_buf + p.o_off, (size_t)p.u.n,
@@ -315,9 +361,14 @@ hc_rc serve_loop(hc_server *srv, const Source &src, double timeout_s, hc_serve_s
     };
     auto admit = [&](hc_request *r) {
         const int64_t id = (int64_t)tr.size();
-        const int64_t c = chunk_keys(srv, *r);
+        Track t{r, 0, 0, r->n > kPackLimit && outputs_locked(srv, *r)};
+        t.in_place = map_in_place(srv, t);
+        // a request whose arrays the kernels use in place needs no slot
+        // buffer, so it is not cut to a slot's size
+        const int64_t c = t.in_place ? r->n : chunk_keys(srv, *r);
         const int64_t units = r->n == 0 ? 1 : (r->n + c - 1) / c;
-        tr.push_back(Track{r, units, 0, r->n > kPackLimit && outputs_locked(srv, *r)});
+        t.units_left = units;
+        tr.push_back(t);
         r->rc = kPending;
         r->done = -1.0;
         for (int64_t k = 0; k < units; ++k) {
@@ -388,7 +439,7 @@ hc_rc serve_loop(hc_server *srv, const Source &src, double timeout_s, hc_serve_s
                 Track &t = tr[(size_t)p.u.req];
                 const hc_request &r = *t.r;
                 --inflight[(size_t)r.table];
-                if (!p.direct_out && p.u.n > 0) {
+                if (!p.in_place && !p.direct_out && p.u.n > 0) {
                     const int vb = val_bytes(srv->tables[r.table]->kind);
                     if (r.h_status) std::memcpy(r.h_status + p.u.off, sl.h_out + p.o_off, (size_t)p.u.n);
                     if (p.vo_off >= 0 && r.h_vals_out)
@@ -455,8 +506,8 @@ hc_rc serve_loop(hc_server *srv, const Source &src, double timeout_s, hc_serve_s
                     if (skipped == nt_none) skipped = j;
                     continue;
                 }
-                int64_t in, out;
-                need(srv, *tr[(size_t)u.req].r, u.n, &in, &out);
+                int64_t in = 0, out = 0;
+                if (!tr[(size_t)u.req].in_place) need(srv, *tr[(size_t)u.req].r, u.n, &in, &out);
                 if (used + in + out > srv->slot_bytes) continue;
                 mode = large ? 2 : 1;
                 batch.push_back(u);

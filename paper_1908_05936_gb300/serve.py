@@ -13,15 +13,18 @@ calling host thread):
    A request is admitted when a free slot of its lane has room for it.  It
    waits otherwise; it is never dropped.
 3. **Dispatch.**  A free slot takes the heads of its lane's FIFOs, one per
-   table, while they fit.  It copies their keys host->device (small requests
-   packed into one copy), runs one batched launch for all of them
-   (`hc_batch_run`, merged mode) or one range call each (plain mode), copies
-   the results device->host and records an event.  Different lanes overlap on
-   the device.
+   table, while they fit, and runs one batched launch for all of them
+   (`hc_batch_run`, merged mode) or one range call each (plain mode), then
+   records an event.  A request whose tensors are all page-locked (as this
+   module makes the results; pin the keys and values) runs in place: the
+   kernels read and write host memory directly, with no copies.  Others are
+   copied host->device (small requests packed into one copy) and back.
+   Different lanes overlap on the device.
 4. **Completion.**  A finished slot hands each request its results and its
    completion time (arrival to the host holding the results).
 
-A request larger than a slot is cut into chunks that run in order; a request
+A request larger than a slot (and not page-locked) is cut into chunks that
+run in order; a request
 with a deadline is dropped (``rc`` = HC_ERR_TIMEOUT, nothing of it runs) if
 it is still waiting for a slot when the deadline passes.  ``run`` serves a
 list of requests with arrival times on the calling thread; ``start`` runs

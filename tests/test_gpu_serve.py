@@ -113,15 +113,18 @@ def _oracle_replay(args):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("inputs", ["pinned", "mixed"])
 @pytest.mark.parametrize("merge", [True, False])
-def test_served_against_oracle(merge):
+def test_served_against_oracle(merge, inputs):
     """A run shaped like the served workload (16 resident map<u64,u64>
     tables prefilled to load factor 0.5; Poisson arrivals of
     insert/find/erase requests 40/50/10 with sizes floor(2^U(0,20)) and
     Zipf(1.1) keys over 2^24 ranks per table; merged and one launch per
     request), against the oracle replaying each table's requests in arrival
     order: every request's statuses, found flags and values, and every
-    table's final contents."""
+    table's final contents.  Page-locked inputs run where they are; with
+    "mixed" every other request's inputs are pageable and go through the
+    slots' staging, so merged launches hold both kinds."""
     from paper_1908_05936_gb300 import build
     build.build()
     n_tables, slots = 16, 1 << 22
@@ -143,9 +146,13 @@ def test_served_against_oracle(merge):
             tabs.append(tab)
         torch.cuda.synchronize()
         reqs = []
-        for q, k in zip(spec, keys):
-            kt = torch.from_numpy(k.view(np.int64)).pin_memory()
-            vt = torch.from_numpy(splitmix.value_of(k).view(np.int64)).pin_memory() if q.op == L.OP_INSERT else None
+        for i, (q, k) in enumerate(zip(spec, keys)):
+            pin = inputs == "pinned" or i % 2 == 0
+            kt = torch.from_numpy(k.view(np.int64).copy())
+            vt = torch.from_numpy(splitmix.value_of(k).view(np.int64)) if q.op == L.OP_INSERT else None
+            if pin:
+                kt = kt.pin_memory()
+                vt = vt.pin_memory() if vt is not None else None
             reqs.append(ServedRequest(q.rid, q.table, q.op, kt, vt, q.arrival))
         srv = Server(tabs, lanes=4, depth=2, merge=merge)
         stats = srv.run(reqs, realtime=True)
@@ -192,7 +199,9 @@ def test_live_submissions_from_two_threads_against_oracle(merge):
     (each submitting the requests of its own half of the tables, so a table's
     arrival order is its thread's order), with requests up to 5x a launch
     slot (cut into chunks); every result and the final contents against the
-    oracle's replay of each table in that order."""
+    oracle's replay of each table in that order.  Every other request has
+    pageable inputs, so those go through the slots' staging (and the large
+    ones are cut into chunks) while the page-locked ones run in place."""
     import threading
     from paper_1908_05936_gb300 import build
     build.build()
@@ -208,14 +217,19 @@ def test_live_submissions_from_two_threads_against_oracle(merge):
         tabs.append(tab)
     torch.cuda.synchronize()
     reqs, per_table = [], [[] for _ in range(n_tables)]
-    for q in spec:
+    for i, q in enumerate(spec):
         k = recipes.zipf_keys(q.table, q.key_stream, q.n, cdf)
         v = splitmix.value_of(k) if q.op == L.OP_INSERT else None
-        reqs.append(ServedRequest(q.rid, q.table, q.op, torch.from_numpy(k.view(np.int64)).pin_memory(),
-                                  torch.from_numpy(v.view(np.int64)).pin_memory() if v is not None else None))
+        kt = torch.from_numpy(k.view(np.int64).copy())
+        vt = torch.from_numpy(v.view(np.int64).copy()) if v is not None else None
+        if i % 2 == 0:
+            kt = kt.pin_memory()
+            vt = vt.pin_memory() if vt is not None else None
+        reqs.append(ServedRequest(q.rid, q.table, q.op, kt, vt))
         per_table[q.table].append((q.rid, q.op, k, v))
     srv = Server(tabs, slot_bytes=1 << 19, lanes=4, depth=2, merge=merge, max_items=8)
-    assert max(q.n for q in spec) * 25 > 5 * (1 << 19)        # some requests need several slots
+    # some pageable requests need several slots
+    assert max(q.n for i, q in enumerate(spec) if i % 2) * 25 > 5 * (1 << 19)
     srv.start()
     errors = []
 
@@ -259,13 +273,17 @@ def test_deadline_drops_only_the_late_request():
                torch.from_numpy(splitmix.value_of(pre[0]).view(np.int64)).cuda(), status=False)
     torch.cuda.synchronize()
 
-    def req(rid, op, keys, deadline=0.0):
+    def req(rid, op, keys, deadline=0.0, pin=True):
         v = splitmix.value_of(keys) if op == L.OP_INSERT else None
-        return ServedRequest(rid, 0, op, torch.from_numpy(keys.view(np.int64)).pin_memory(),
-                             torch.from_numpy(v.view(np.int64)).pin_memory() if v is not None else None,
-                             deadline=deadline)
+        kt = torch.from_numpy(keys.view(np.int64).copy())
+        vt = torch.from_numpy(v.view(np.int64).copy()) if v is not None else None
+        if pin:
+            kt = kt.pin_memory()
+            vt = vt.pin_memory() if vt is not None else None
+        return ServedRequest(rid, 0, op, kt, vt, deadline=deadline)
 
-    big = req(0, L.OP_INSERT, splitmix.stream_u64(7201, 0, 0, 1 << 21))          # about 50 chunks of 1 MiB
+    # pageable inputs: staged through the slot, about 50 chunks of 1 MiB
+    big = req(0, L.OP_INSERT, splitmix.stream_u64(7201, 0, 0, 1 << 21), pin=False)
     late = [req(1 + i, L.OP_INSERT, splitmix.stream_u64(7300 + i, 0, 0, 1000), deadline=1e-4) for i in range(3)]
     calm = req(4, L.OP_FIND, np.concatenate([pre[0][:500], late[0].keys.numpy().view(np.uint64)[:500]]))
     srv = Server([tab], slot_bytes=1 << 20, lanes=1, depth=1, merge=True)
